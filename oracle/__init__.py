@@ -1,0 +1,214 @@
+"""CPU oracle of the AGILE I/O path (arXiv 2504.19365) -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+may import this package.  It shares no code with the CUDA library and never imports it.
+The arithmetic lives in ``agile_oracle.c`` (compiled by ``oracle/build.py``); this
+module only marshals numpy arrays through ctypes.
+
+Functions and the passage each restates:
+  store_read_page / store_write_page -- 4 KiB page store (Sec. 2.3.3)
+  RefCache                          -- sequential set-associative clock cache with the
+                                       line states of Sec. 3.4 and the clock policy of
+                                       Sec. 4.4
+  embedding_bag / _backward / sgd   -- sum-pooled lookups of Sec. 4.4, fixed order
+  bfs                               -- FIFO-queue BFS over CSR (Sec. 4.5)
+  ideal_speedup                     -- Eq. 1
+  set_of                            -- the cache's set-index function
+
+Parity status: every function above is pinned by ``tests/test_oracle_*.py`` against
+closed forms, brute force, library routines (torch, scipy) or hand-derived golden
+traces.  The paper's own speedup figures (RTX 5000 Ada, Gen4 SSDs, BaM) are not
+computed here: parity unpinned for those by construction.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import build as _build
+
+PAGE = 4096
+INVALID, BUSY, READY, MODIFIED = 0, 1, 2, 3
+HIT, MISS_FILL, MISS_EVICT, MISS_WRITEBACK = 0, 1, 2, 3
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        vp, u64, u32, i32 = C.c_void_p, C.c_uint64, C.c_uint32, C.c_int32
+        L.orc_store_read_page.argtypes = [vp, u64, vp]
+        L.orc_store_write_page.argtypes = [vp, u64, vp]
+        L.orc_set_of.argtypes = [u64, u32]
+        L.orc_set_of.restype = u32
+        L.orc_cache_new.argtypes = [u32, u32, u64]
+        L.orc_cache_new.restype = vp
+        L.orc_cache_free.argtypes = [vp]
+        L.orc_cache_lookup.argtypes = [vp, vp, u64, C.POINTER(u32), C.POINTER(u64)]
+        L.orc_cache_lookup.restype = C.c_int
+        L.orc_cache_read.argtypes = [vp, vp, u64, u32, u32, vp]
+        L.orc_cache_read.restype = C.c_int
+        L.orc_cache_write.argtypes = [vp, vp, u64, u32, u32, vp, C.c_int]
+        L.orc_cache_write.restype = C.c_int
+        L.orc_cache_flush.argtypes = [vp, vp]
+        L.orc_cache_flush.restype = u64
+        L.orc_cache_replay.argtypes = [vp, vp, vp, u64, vp]
+        L.orc_cache_counters.argtypes = [vp, vp]
+        L.orc_cache_wb_log.argtypes = [vp, vp, u64]
+        L.orc_cache_wb_log.restype = u64
+        L.orc_cache_tags.argtypes = [vp, vp, vp, vp]
+        L.orc_cache_line.argtypes = [vp, u64, vp]
+        L.orc_embedding_bag.argtypes = [vp, u64, u32, vp, vp, u64, vp]
+        L.orc_embedding_bag_backward.argtypes = [u64, u32, vp, vp, u64, vp, vp, vp]
+        L.orc_sgd.argtypes = [vp, u64, u32, vp, vp, C.c_float]
+        L.orc_bfs.argtypes = [u64, vp, vp, i32, vp]
+        L.orc_bfs.restype = u64
+        L.orc_ideal_speedup.argtypes = [C.c_double]
+        L.orc_ideal_speedup.restype = C.c_double
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# ----------------------------------------------------------------------------- store
+
+def store_read_page(store: np.ndarray, page: int) -> np.ndarray:
+    out = np.empty(PAGE, dtype=np.uint8)
+    lib().orc_store_read_page(_p(store), page, _p(out))
+    return out
+
+
+def store_write_page(store: np.ndarray, page: int, data: np.ndarray) -> None:
+    d = _c(data, np.uint8)
+    assert d.size == PAGE
+    lib().orc_store_write_page(_p(store), page, _p(d))
+
+
+def set_of(page: int, sets: int) -> int:
+    return int(lib().orc_set_of(page, sets))
+
+
+# ----------------------------------------------------------------------------- cache
+
+class RefCache:
+    """Sequential reference cache; ``store`` is a uint8 numpy array the cache reads on
+    fills and writes on write-backs (it is modified in place)."""
+
+    def __init__(self, sets: int, ways: int, store: np.ndarray, wb_cap: int = 1 << 20):
+        assert store.dtype == np.uint8 and store.flags.c_contiguous
+        self.sets, self.ways, self.store = sets, ways, store
+        self.h = lib().orc_cache_new(sets, ways, wb_cap)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_cache_free(self.h)
+            self.h = None
+
+    def lookup(self, page: int):
+        w = C.c_uint32()
+        v = C.c_uint64()
+        code = lib().orc_cache_lookup(self.h, _p(self.store), page, C.byref(w), C.byref(v))
+        return code, int(w.value), int(v.value)
+
+    def read(self, page: int, off: int = 0, length: int = PAGE) -> tuple[int, np.ndarray]:
+        out = np.empty(length, dtype=np.uint8)
+        code = lib().orc_cache_read(self.h, _p(self.store), page, off, length, _p(out))
+        return code, out
+
+    def write(self, page: int, off: int, data: np.ndarray, write_through: bool = False) -> int:
+        d = _c(data, np.uint8)
+        return lib().orc_cache_write(self.h, _p(self.store), page, off, d.size, _p(d),
+                                     1 if write_through else 0)
+
+    def flush(self) -> int:
+        return int(lib().orc_cache_flush(self.h, _p(self.store)))
+
+    def replay(self, pages) -> np.ndarray:
+        p = _c(pages, np.uint64)
+        codes = np.empty(p.size, dtype=np.int32)
+        lib().orc_cache_replay(self.h, _p(self.store), _p(p), p.size, _p(codes))
+        return codes
+
+    def counters(self) -> dict:
+        out = np.zeros(4, dtype=np.uint64)
+        lib().orc_cache_counters(self.h, _p(out))
+        return dict(hits=int(out[0]), misses=int(out[1]), evictions=int(out[2]),
+                    writebacks=int(out[3]))
+
+    def writeback_log(self) -> np.ndarray:
+        n = int(lib().orc_cache_wb_log(self.h, None, 0))
+        out = np.zeros(max(n, 1), dtype=np.uint64)
+        lib().orc_cache_wb_log(self.h, _p(out), n)
+        return out[:n]
+
+    def tags(self):
+        n = self.sets * self.ways
+        page = np.zeros(n, dtype=np.uint64)
+        state = np.zeros(n, dtype=np.uint8)
+        ref = np.zeros(n, dtype=np.uint8)
+        lib().orc_cache_tags(self.h, _p(page), _p(state), _p(ref))
+        return page, state, ref
+
+    def line(self, line: int) -> np.ndarray:
+        out = np.empty(PAGE, dtype=np.uint8)
+        lib().orc_cache_line(self.h, line, _p(out))
+        return out
+
+
+# ----------------------------------------------------------------------------- embedding bag
+
+def embedding_bag(table: np.ndarray, idx: np.ndarray, offsets: np.ndarray) -> np.ndarray:
+    t = _c(table, np.float32)
+    i = _c(idx, np.int64)
+    o = _c(offsets, np.int64)
+    rows, dim = t.shape
+    nb = o.size - 1
+    out = np.empty((nb, dim), dtype=np.float32)
+    lib().orc_embedding_bag(_p(t), rows, dim, _p(i), _p(o), nb, _p(out))
+    return out
+
+
+def embedding_bag_backward(rows: int, idx, offsets, gout: np.ndarray):
+    g = _c(gout, np.float32)
+    i = _c(idx, np.int64)
+    o = _c(offsets, np.int64)
+    nb, dim = g.shape
+    G = np.empty((rows, dim), dtype=np.float32)
+    touched = np.empty(rows, dtype=np.uint8)
+    lib().orc_embedding_bag_backward(rows, dim, _p(i), _p(o), nb, _p(g), _p(G), _p(touched))
+    return G, touched
+
+
+def sgd(table: np.ndarray, G: np.ndarray, touched: np.ndarray, lr: float) -> np.ndarray:
+    t = np.array(table, dtype=np.float32, copy=True, order="C")
+    g = _c(G, np.float32)
+    tc = _c(touched, np.uint8)
+    rows, dim = t.shape
+    lib().orc_sgd(_p(t), rows, dim, _p(g), _p(tc), lr)
+    return t
+
+
+# ----------------------------------------------------------------------------- BFS
+
+def bfs(offsets: np.ndarray, cols: np.ndarray, src: int):
+    o = _c(offsets, np.int64)
+    c = _c(cols, np.int32)
+    n = o.size - 1
+    level = np.empty(max(n, 1), dtype=np.int32)
+    scanned = int(lib().orc_bfs(n, _p(o), _p(c), int(src), _p(level)))
+    return level[:n], scanned
+
+
+def ideal_speedup(ctc: float) -> float:
+    return float(lib().orc_ideal_speedup(ctc))

@@ -1,0 +1,328 @@
+/*
+ * CPU oracle for the AGILE asynchronous GPU-SSD I/O path (arXiv 2504.19365).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or call this
+ * file: only the test-suite, the smoke check and the CPU-baseline leg of the benchmark
+ * use it.  It shares no code, header or table with the CUDA library.
+ *
+ * Plain, slow, sequential C.  Every function restates a definition from the paper (or,
+ * where the paper is silent, the reading recorded in the design notes) without any
+ * blocking, fusion or reordering:
+ *
+ *   - page store          : a flat byte array addressed in 4 KiB pages (Sec. 2.3.3: flash
+ *                           is managed in 4 KB pages and cache lines align with them).
+ *   - reference cache     : a sequential set-associative software cache with the line
+ *                           states of Sec. 3.4 (INVALID / READY / MODIFIED; BUSY is never
+ *                           observable when requests are served one at a time) and clock
+ *                           replacement (Sec. 4.4 names the clock policy of Corbato 1968).
+ *   - embedding bag       : sum pooling of table rows, one FP32 accumulator per output
+ *                           element, indices added in increasing order (Sec. 4.4 DLRM
+ *                           lookups); backward scatter-add and an SGD step.
+ *   - BFS                 : textbook FIFO-queue breadth-first search over CSR (Sec. 4.5).
+ *   - ideal speedup       : Eq. 1.
+ *
+ * Floating point: compiled with -ffp-contract=off so that a*b+c is never fused.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PAGE 4096u
+
+/* ------------------------------------------------------------------ page store */
+
+/* Read page p of the store (Sec. 2.3.3: the store is addressed in 4 KiB pages). */
+void orc_store_read_page(const uint8_t *store, uint64_t page, uint8_t *out) {
+  memcpy(out, store + page * ORC_PAGE, ORC_PAGE);
+}
+
+void orc_store_write_page(uint8_t *store, uint64_t page, const uint8_t *in) {
+  memcpy(store + page * ORC_PAGE, in, ORC_PAGE);
+}
+
+/* ------------------------------------------------------------------ reference cache */
+
+enum { ORC_INVALID = 0, ORC_BUSY = 1, ORC_READY = 2, ORC_MODIFIED = 3 };
+
+enum {
+  ORC_HIT = 0,          /* case (a): READY or MODIFIED line holds the page           */
+  ORC_MISS_FILL = 1,    /* case (b): an INVALID way is filled                         */
+  ORC_MISS_EVICT = 2,   /* case (d): a READY victim is reset and refilled             */
+  ORC_MISS_WRITEBACK = 3 /* case (d): a MODIFIED victim is written back, then refilled */
+};
+
+typedef struct {
+  uint32_t sets, ways;
+  uint64_t *page;   /* [sets*ways] page held by the way                    */
+  uint8_t *state;   /* [sets*ways] ORC_INVALID / ORC_READY / ORC_MODIFIED  */
+  uint8_t *ref;     /* [sets*ways] clock reference bit                     */
+  uint32_t *hand;   /* [sets] clock hand                                   */
+  uint8_t *data;    /* [sets*ways*4096] line contents                      */
+  uint64_t hits, misses, evictions, writebacks;
+  uint64_t *wb_log; /* pages written back, in order                         */
+  uint64_t wb_cap, wb_len;
+} orc_cache;
+
+/* Set index of a page: the 64-bit golden-ratio multiplicative hash, whose upper 32
+ * bits are reduced to [0, sets) by a multiply-shift.  Any number of sets works. */
+uint32_t orc_set_of(uint64_t page, uint32_t sets) {
+  uint64_t h = page * 0x9E3779B97F4A7C15ull;
+  return (uint32_t)(((h >> 32) * (uint64_t)sets) >> 32);
+}
+
+orc_cache *orc_cache_new(uint32_t sets, uint32_t ways, uint64_t wb_cap) {
+  orc_cache *c = (orc_cache *)calloc(1, sizeof(orc_cache));
+  uint64_t n = (uint64_t)sets * ways;
+  c->sets = sets;
+  c->ways = ways;
+  c->page = (uint64_t *)calloc(n, sizeof(uint64_t));
+  c->state = (uint8_t *)calloc(n, 1);
+  c->ref = (uint8_t *)calloc(n, 1);
+  c->hand = (uint32_t *)calloc(sets, sizeof(uint32_t));
+  c->data = (uint8_t *)calloc(n, ORC_PAGE);
+  c->wb_cap = wb_cap;
+  c->wb_log = (uint64_t *)calloc(wb_cap ? wb_cap : 1, sizeof(uint64_t));
+  return c;
+}
+
+void orc_cache_free(orc_cache *c) {
+  if (!c) return;
+  free(c->page); free(c->state); free(c->ref); free(c->hand); free(c->data); free(c->wb_log);
+  free(c);
+}
+
+static void orc_log_wb(orc_cache *c, uint64_t page) {
+  if (c->wb_len < c->wb_cap) c->wb_log[c->wb_len] = page;
+  c->wb_len++;
+  c->writebacks++;
+}
+
+/*
+ * One request for `page`, served to completion before the next (Sec. 3.4 cases):
+ *   (a) a way holds the page in READY or MODIFIED           -> hit, reference bit set;
+ *   (b) otherwise the lowest INVALID way of the set is filled from the store;
+ *   (d) otherwise the clock picks a victim: starting at the set's hand, a way whose
+ *       reference bit is set has it cleared and the hand moves on; the first way with a
+ *       clear bit is the victim and the hand moves past it.  A MODIFIED victim is written
+ *       back to the store first.  The filled line gets its reference bit set.
+ * On return *way_out is the way now holding the page and the code says which case ran.
+ * `store` is read on a fill and written on a write-back.
+ */
+int orc_cache_lookup(orc_cache *c, uint8_t *store, uint64_t page, uint32_t *way_out,
+                     uint64_t *victim_page) {
+  uint32_t s = orc_set_of(page, c->sets);
+  uint64_t base = (uint64_t)s * c->ways;
+  for (uint32_t w = 0; w < c->ways; ++w) {
+    uint8_t st = c->state[base + w];
+    if ((st == ORC_READY || st == ORC_MODIFIED) && c->page[base + w] == page) {
+      c->ref[base + w] = 1;
+      c->hits++;
+      *way_out = w;
+      return ORC_HIT;
+    }
+  }
+  c->misses++;
+  int code = ORC_MISS_FILL;
+  uint32_t victim = c->ways;
+  for (uint32_t w = 0; w < c->ways; ++w) {
+    if (c->state[base + w] == ORC_INVALID) { victim = w; break; }
+  }
+  if (victim == c->ways) {
+    /* clock sweep: at most one full pass clears every bit, the next step finds a 0 */
+    for (uint32_t step = 0; step < 2 * c->ways + 1; ++step) {
+      uint32_t w = c->hand[s];
+      c->hand[s] = (w + 1) % c->ways;
+      if (c->ref[base + w]) {
+        c->ref[base + w] = 0;
+      } else {
+        victim = w;
+        break;
+      }
+    }
+    uint64_t old = c->page[base + victim];
+    if (victim_page) *victim_page = old;
+    c->evictions++;
+    if (c->state[base + victim] == ORC_MODIFIED) {
+      memcpy(store + old * ORC_PAGE, c->data + (base + victim) * ORC_PAGE, ORC_PAGE);
+      orc_log_wb(c, old);
+      code = ORC_MISS_WRITEBACK;
+    } else {
+      code = ORC_MISS_EVICT;
+    }
+  }
+  memcpy(c->data + (base + victim) * ORC_PAGE, store + page * ORC_PAGE, ORC_PAGE);
+  c->page[base + victim] = page;
+  c->state[base + victim] = ORC_READY;
+  c->ref[base + victim] = 1;
+  *way_out = victim;
+  return code;
+}
+
+/* Read `len` bytes at byte offset `off` inside `page` through the cache. */
+int orc_cache_read(orc_cache *c, uint8_t *store, uint64_t page, uint32_t off, uint32_t len,
+                   uint8_t *out) {
+  uint32_t w;
+  int code = orc_cache_lookup(c, store, page, &w, NULL);
+  uint64_t line = (uint64_t)orc_set_of(page, c->sets) * c->ways + w;
+  memcpy(out, c->data + line * ORC_PAGE + off, len);
+  return code;
+}
+
+/*
+ * Write `len` bytes at byte offset `off` of `page` through the cache.
+ * write_through = 0: write-back policy, the line becomes MODIFIED (Sec. 3.4 case (d)
+ *                    writes it back on eviction).
+ * write_through = 1: the line is updated and the page is written to the store at once,
+ *                    the line stays READY (Sec. 3.5: an async write updates the cache
+ *                    and issues the write command).
+ * A missing page is first filled from the store (write-allocate).
+ */
+int orc_cache_write(orc_cache *c, uint8_t *store, uint64_t page, uint32_t off, uint32_t len,
+                    const uint8_t *in, int write_through) {
+  uint32_t w;
+  int code = orc_cache_lookup(c, store, page, &w, NULL);
+  uint64_t line = (uint64_t)orc_set_of(page, c->sets) * c->ways + w;
+  memcpy(c->data + line * ORC_PAGE + off, in, len);
+  if (write_through) {
+    memcpy(store + page * ORC_PAGE, c->data + line * ORC_PAGE, ORC_PAGE);
+    if (c->state[line] != ORC_MODIFIED) c->state[line] = ORC_READY;
+  } else {
+    c->state[line] = ORC_MODIFIED;
+  }
+  return code;
+}
+
+/* Write every MODIFIED line back, in line order, and mark it READY. */
+uint64_t orc_cache_flush(orc_cache *c, uint8_t *store) {
+  uint64_t n = (uint64_t)c->sets * c->ways, cnt = 0;
+  for (uint64_t l = 0; l < n; ++l) {
+    if (c->state[l] == ORC_MODIFIED) {
+      memcpy(store + c->page[l] * ORC_PAGE, c->data + l * ORC_PAGE, ORC_PAGE);
+      orc_log_wb(c, c->page[l]);
+      c->state[l] = ORC_READY;
+      cnt++;
+    }
+  }
+  return cnt;
+}
+
+/* Replay a trace of page reads; outcome codes go to codes[i] (may be NULL). */
+void orc_cache_replay(orc_cache *c, uint8_t *store, const uint64_t *pages, uint64_t n,
+                      int32_t *codes) {
+  for (uint64_t i = 0; i < n; ++i) {
+    uint32_t w;
+    int code = orc_cache_lookup(c, store, pages[i], &w, NULL);
+    if (codes) codes[i] = code;
+  }
+}
+
+void orc_cache_counters(const orc_cache *c, uint64_t out[4]) {
+  out[0] = c->hits; out[1] = c->misses; out[2] = c->evictions; out[3] = c->writebacks;
+}
+
+uint64_t orc_cache_wb_log(const orc_cache *c, uint64_t *out, uint64_t cap) {
+  uint64_t n = c->wb_len < c->wb_cap ? c->wb_len : c->wb_cap;
+  if (n > cap) n = cap;
+  memcpy(out, c->wb_log, n * sizeof(uint64_t));
+  return c->wb_len;
+}
+
+/* Export tags: page[l], state[l], ref[l] for every line l = set*ways + way. */
+void orc_cache_tags(const orc_cache *c, uint64_t *page, uint8_t *state, uint8_t *ref) {
+  uint64_t n = (uint64_t)c->sets * c->ways;
+  memcpy(page, c->page, n * sizeof(uint64_t));
+  memcpy(state, c->state, n);
+  memcpy(ref, c->ref, n);
+}
+
+void orc_cache_line(const orc_cache *c, uint64_t line, uint8_t *out) {
+  memcpy(out, c->data + line * ORC_PAGE, ORC_PAGE);
+}
+
+/* ------------------------------------------------------------------ embedding bag */
+
+/*
+ * Sum-pooled embedding bag: out[b, d] = sum over i in [off[b], off[b+1]) of T[idx[i], d],
+ * one FP32 accumulator per (b, d) starting at +0.0, indices added in increasing i.
+ */
+void orc_embedding_bag(const float *table, uint64_t rows, uint32_t dim, const int64_t *idx,
+                       const int64_t *off, uint64_t n_bags, float *out) {
+  (void)rows;
+  for (uint64_t b = 0; b < n_bags; ++b) {
+    for (uint32_t d = 0; d < dim; ++d) {
+      float acc = 0.0f;
+      for (int64_t i = off[b]; i < off[b + 1]; ++i) acc = acc + table[(uint64_t)idx[i] * dim + d];
+      out[b * dim + d] = acc;
+    }
+  }
+}
+
+/*
+ * Backward of the sum-pooled bag: G[r, d] = sum over every (b, i) with idx[i] = r of
+ * gout[b, d], added in increasing (b, i) order into one FP32 accumulator per (r, d)
+ * starting at +0.0.  touched[r] = 1 for each row that occurs.
+ */
+void orc_embedding_bag_backward(uint64_t rows, uint32_t dim, const int64_t *idx,
+                                const int64_t *off, uint64_t n_bags, const float *gout,
+                                float *G, uint8_t *touched) {
+  memset(G, 0, rows * dim * sizeof(float));
+  memset(touched, 0, rows);
+  for (uint64_t b = 0; b < n_bags; ++b) {
+    for (int64_t i = off[b]; i < off[b + 1]; ++i) {
+      uint64_t r = (uint64_t)idx[i];
+      touched[r] = 1;
+      for (uint32_t d = 0; d < dim; ++d) G[r * dim + d] = G[r * dim + d] + gout[b * dim + d];
+    }
+  }
+}
+
+/* SGD on the touched rows: T[r, d] = T[r, d] - (lr * G[r, d]), product rounded first. */
+void orc_sgd(float *table, uint64_t rows, uint32_t dim, const float *G, const uint8_t *touched,
+             float lr) {
+  for (uint64_t r = 0; r < rows; ++r) {
+    if (!touched[r]) continue;
+    for (uint32_t d = 0; d < dim; ++d) {
+      float step = lr * G[r * dim + d];
+      table[r * dim + d] = table[r * dim + d] - step;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------ BFS */
+
+/*
+ * Textbook breadth-first search with a FIFO queue over a CSR graph.
+ * level[src] = 0, level[v] = level[u] + 1 for the first u that discovers v, -1 when
+ * unreachable.  Returns the number of CSR entries scanned: the sum of the degrees of
+ * every reached vertex (each vertex is dequeued once and scans its whole list).
+ */
+uint64_t orc_bfs(uint64_t n, const int64_t *offsets, const int32_t *cols, int32_t src,
+                 int32_t *level) {
+  for (uint64_t v = 0; v < n; ++v) level[v] = -1;
+  if (n == 0 || src < 0 || (uint64_t)src >= n) return 0;
+  int32_t *queue = (int32_t *)malloc(n * sizeof(int32_t));
+  uint64_t head = 0, tail = 0, scanned = 0;
+  level[src] = 0;
+  queue[tail++] = src;
+  while (head < tail) {
+    int32_t u = queue[head++];
+    for (int64_t e = offsets[u]; e < offsets[u + 1]; ++e) {
+      int32_t v = cols[e];
+      scanned++;
+      if (level[v] < 0) {
+        level[v] = level[u] + 1;
+        queue[tail++] = v;
+      }
+    }
+  }
+  free(queue);
+  return scanned;
+}
+
+/* ------------------------------------------------------------------ Eq. 1 */
+
+/* Ideal overlap speedup of Eq. 1: 1 + CTC for 0 <= CTC <= 1, else 1 + 1/CTC. */
+double orc_ideal_speedup(double ctc) {
+  if (ctc < 0) return 0.0 / 0.0;
+  return ctc <= 1.0 ? 1.0 + ctc : 1.0 + 1.0 / ctc;
+}
