@@ -1,0 +1,219 @@
+/*
+ * agile.h -- C-ABI of a GB300 (sm_103a) library for asynchronous GPU-centric page I/O
+ * through an HBM software cache, after "AGILE: Lightweight and Efficient Asynchronous
+ * GPU-SSD Integration" (arXiv 2504.19365).
+ *
+ * What the library computes (paper section in brackets):
+ *   - NVMe-style submission/completion queue pairs held in HBM, filled by GPU threads
+ *     that also write the tail doorbells themselves [Sec. 2.1, Sec. 3.3.1, Alg. 2];
+ *   - a service role that polls completion queues one 32-entry window per warp and
+ *     releases queue slots and per-request completion tokens [Sec. 3.2, Alg. 1];
+ *   - a set-associative software cache of 4 KiB lines in HBM with the line states
+ *     INVALID / BUSY / READY / MODIFIED and clock replacement [Sec. 3.4, Sec. 4.4];
+ *   - warp-level and cache-level coalescing of requests for one page [Sec. 3.3.2];
+ *   - an in-flight share table (page -> request in flight) [Sec. 3.4.1];
+ *   - issue / continue / wait with completion tokens: no thread waits for a completion
+ *     while it holds a queue slot or a cache line [Sec. 2.3.1, Sec. 2.3.2, Sec. 3.2.1];
+ *   - two drivers: sum-pooled embedding-bag lookups [Sec. 4.4] and a CSR breadth-first
+ *     search [Sec. 4.5], each in a synchronous mode (issue then stall) and an
+ *     asynchronous mode (issue ahead, continue, wait later) [Sec. 4.2, Sec. 4.4].
+ *
+ * The backing store is an emulated NVMe device: its data lives in pinned host memory
+ * (reached over the host link), it consumes the 64-byte submission entries from the
+ * HBM rings, copies 4 KiB pages between host memory and HBM, and posts 16-byte
+ * completion entries with a phase bit.  Its latency and per-queue throughput are
+ * configurable.  The device is emulated by warps of the same kernel launch that runs
+ * the work, so it makes progress only while a library call is executing on the GPU;
+ * every call drains the commands it issued before it returns on its stream.
+ *
+ * Conventions
+ *   - Ownership: the library owns the cache, queues, tokens, staging buffers and the
+ *     pinned store.  The caller owns every buffer whose name starts with d_ (device
+ *     memory, e.g. a torch tensor's data pointer) and every stream (a cudaStream_t
+ *     passed as void*; NULL = legacy default stream).
+ *   - Launches are asynchronous on `stream`.  A return value of 0 means the launch
+ *     was accepted; errors found on the GPU (timeouts, device errors) are reported
+ *     per token by agile_wait and sticky per context by agile_check.
+ *   - Errors: 0 on success, else a negative AGILE_E* code.  Pointers that must not be
+ *     NULL give AGILE_EINVAL.
+ *   - One context may be used by one stream at a time; calls that overlap on the GPU
+ *     for the same context race on its queues and cache.
+ */
+#ifndef AGILE_H
+#define AGILE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define AGILE_API __attribute__((visibility("default")))
+#else
+#define AGILE_API
+#endif
+
+#define AGILE_PAGE_SIZE 4096u
+
+/* error codes (negative) */
+#define AGILE_OK 0
+#define AGILE_EIO (-5)          /* a command completed with a non-zero status         */
+#define AGILE_EAGAIN (-11)      /* no line or queue slot free right now               */
+#define AGILE_ENOMEM (-12)      /* allocation failed                                  */
+#define AGILE_ENODEV (-19)      /* no CUDA device / requested backing device absent   */
+#define AGILE_EINVAL (-22)      /* bad argument                                       */
+#define AGILE_ETIMEDOUT (-110)  /* a bounded wait on the GPU ran out                  */
+#define AGILE_ECUDA (-1000)     /* a CUDA runtime call failed                         */
+
+/* modes of the application drivers */
+#define AGILE_SYNC 0u   /* each page is requested when needed and waited for at once */
+#define AGILE_ASYNC 1u  /* pages are requested ahead, work continues, waits come later */
+
+/* emulator fault injection flags (host-configured; no GPU fault is ever raised) */
+#define AGILE_FAULT_EIO 1u        /* complete a fraction of commands with an error    */
+#define AGILE_FAULT_DROP_CQE 2u   /* never post the completion of a fraction of them  */
+
+/* token of a request: {queue:16 | slot:16 | ticket:32}; AGILE_TOKEN_HIT = served from
+ * the cache without a command of its own */
+typedef uint64_t agile_token;
+#define AGILE_TOKEN_HIT (~(uint64_t)0)
+
+typedef struct agile_ctx agile_ctx;
+
+typedef struct {
+  uint64_t store_bytes;     /* backing store size, multiple of 4096                    */
+  const char *nvme_path;    /* NULL: emulated device (the only backend built)         */
+  uint64_t cache_bytes;     /* HBM cache size; rounded down to ways*4096 multiples    */
+  uint32_t ways;            /* associativity, 1..32                                   */
+  uint32_t num_queues;      /* queue pairs, 1..65535                                  */
+  uint32_t queue_depth;     /* entries per queue, power of two in [64, 65536]         */
+  uint32_t emu_latency_ns;  /* per-command device latency (0 = none)                  */
+  double emu_queue_gbps;    /* per-queue throughput cap in GB/s (0 = uncapped)        */
+  uint64_t wait_timeout_ns; /* bound on every wait inside a call (0 = 10 s)           */
+  int32_t device;           /* CUDA device ordinal                                    */
+  uint32_t fault_flags;     /* AGILE_FAULT_* (0 = none)                               */
+  double fault_rate;        /* fraction of commands hit by the injected fault         */
+  uint64_t seed;            /* seed of the fault injector                             */
+  uint32_t max_ctas;        /* cap on CTAs per launch (0 = all co-resident CTAs)      */
+  uint32_t prefetch_depth;  /* async lookahead in work units (0 = default 1)          */
+} agile_config;
+
+typedef struct {
+  uint64_t hits;            /* requests served by a READY/MODIFIED line (case a)      */
+  uint64_t misses;          /* requests that issued a read (cases b, d)              */
+  uint64_t busy_hits;       /* requests that found their page in flight (case c)     */
+  uint64_t warp_coalesced;  /* requests merged by the warp-level match              */
+  uint64_t share_retries;   /* misses deferred because the page's entry was taken    */
+  uint64_t evictions;       /* valid victims replaced                                */
+  uint64_t writebacks;      /* MODIFIED lines written back                           */
+  uint64_t eagain;          /* victim searches that found nothing evictable          */
+  uint64_t sq_full;         /* reservations that found every queue full             */
+  uint64_t doorbells;       /* SQ tail doorbell writes                               */
+  uint64_t commands;        /* commands consumed by the device                       */
+  uint64_t cqes;            /* completions consumed by the pollers                   */
+  uint64_t cq_doorbells;    /* CQ head doorbell writes (one per 32-entry window)     */
+  uint64_t io_errors;       /* completions with a non-zero status                    */
+  uint64_t bytes_read;      /* bytes the device moved store -> HBM                   */
+  uint64_t bytes_written;   /* bytes the device moved HBM -> store                   */
+  uint64_t prefetches;      /* prefetch requests issued                              */
+  uint64_t timeouts;        /* bounded waits that ran out                            */
+} agile_stats_t;
+
+/* Fill *cfg with defaults: 128 queue pairs x 256 entries (Sec. 4.4 default), 8 ways,
+ * no latency model, 10 s wait bound, device 0. */
+AGILE_API void agile_config_default(agile_config *cfg);
+
+/* Host initialisation (Listing 1 host side, Sec. 3.1): allocates the pinned store, the
+ * HBM cache, the queue rings and the service state on cfg->device.  *out receives
+ * the context.  AGILE_ENODEV if cfg->nvme_path is non-NULL (no real NVMe backend). */
+AGILE_API int agile_init(const agile_config *cfg, agile_ctx **out);
+
+/* Drain, flush MODIFIED lines to the store and free everything.  NULL is a no-op. */
+AGILE_API int agile_destroy(agile_ctx *ctx);
+
+/* Copy n bytes between host memory and the backing store at byte offset off
+ * (host side, synchronous; the device is idle in between calls).  Cached lines of
+ * the pages touched by agile_store_write are invalidated first, MODIFIED ones are
+ * written back before.  AGILE_EINVAL if [off, off+n) leaves the store. */
+AGILE_API int agile_store_write(agile_ctx *ctx, uint64_t off, const void *host_src, uint64_t n);
+AGILE_API int agile_store_read(agile_ctx *ctx, uint64_t off, void *host_dst, uint64_t n);
+
+/* asyncRead (Sec. 3.1, Listing 1 Method-2): for i < n, copy store page d_pages[i]
+ * through the cache into d_dst + i*4096 and write its token to d_tok[i] (may be
+ * NULL).  d_pages: uint64 page numbers; d_dst: n*4096 bytes, 16-byte aligned.
+ * mode AGILE_ASYNC issues all misses of a warp's pages before waiting for any. */
+AGILE_API int agile_read_async(agile_ctx *ctx, const uint64_t *d_pages, uint32_t n, void *d_dst,
+                     agile_token *d_tok, uint32_t mode, void *stream);
+
+/* asyncWrite (Sec. 3.5): for i < n, write d_src + i*4096 to store page d_pages[i]:
+ * the cache line is updated and a write command is issued from a staging copy.
+ * Pages must be distinct within one call. */
+AGILE_API int agile_write_async(agile_ctx *ctx, const uint64_t *d_pages, uint32_t n,
+                      const void *d_src, agile_token *d_tok, void *stream);
+
+/* wait (Sec. 3.2.1 "lock a"): d_status[i] = 0 when token i completed cleanly,
+ * AGILE_EIO when it completed with an error, AGILE_ETIMEDOUT when it is still
+ * outstanding after cfg->wait_timeout_ns. */
+AGILE_API int agile_wait(agile_ctx *ctx, const agile_token *d_tok, uint32_t n, int32_t *d_status,
+               void *stream);
+
+/* prefetch (Sec. 3.1): start filling the cache with store pages d_pages[0..n). */
+AGILE_API int agile_prefetch(agile_ctx *ctx, const uint64_t *d_pages, uint32_t n, void *stream);
+
+/* Write every MODIFIED line back to the store (Sec. 3.4 case (d) write-back). */
+AGILE_API int agile_flush(agile_ctx *ctx, void *stream);
+
+/* Drop every line (flushes MODIFIED lines first); the next requests start cold. */
+AGILE_API int agile_invalidate(agile_ctx *ctx, void *stream);
+
+/* Sum-pooled embedding bag (Sec. 4.4): the table is `rows` x `dim` FP32 stored
+ * row-major at byte table_byte0 of the store (multiple of 4096; dim a multiple of 4,
+ * dim*4 <= 4096).  d_out[b*dim + d] = sum over i in [d_offsets[b], d_offsets[b+1])
+ * of T[d_idx[i]][d], added in increasing i in FP32 (round to nearest, no fusion).
+ * d_idx, d_offsets: int64; d_out: n_bags*dim floats.  Indices outside [0, rows) make
+ * the call fail with AGILE_EINVAL reported through agile_check. */
+AGILE_API int agile_embedding_bag(agile_ctx *ctx, uint64_t table_byte0, uint32_t rows, uint32_t dim,
+                        const int64_t *d_idx, const int64_t *d_offsets, uint32_t n_bags,
+                        float *d_out, uint32_t mode, void *stream);
+
+/* Breadth-first search over a CSR graph on the store (Sec. 4.5): int64 offsets
+ * [n_vertices+1] at byte offsets_byte0, int32 columns at byte cols_byte0 (both
+ * multiples of 4096).  d_level[v] = BFS level of v from src, -1 when unreachable.
+ * *d_edges_scanned (uint64, device, may be NULL) = sum of the degrees of every
+ * reached vertex.  Top-down, level-synchronous; mode as above. */
+AGILE_API int agile_bfs(agile_ctx *ctx, uint64_t offsets_byte0, uint64_t cols_byte0,
+              uint32_t n_vertices, int32_t src, int32_t *d_level,
+              uint64_t *d_edges_scanned, uint32_t mode, void *stream);
+
+/* Validation entry point: serve store pages d_pages[0..n) one at a time, in order, by
+ * a single GPU thread (sync mode), and write the outcome of each request to
+ * d_codes[i] (0 hit, 1 fill of an INVALID way, 2 eviction of a READY line, 3
+ * write-back of a MODIFIED line).  With one request in flight the cache must behave
+ * exactly like the sequential reference cache of Sec. 3.4 / Sec. 4.4. */
+AGILE_API int agile_cache_replay(agile_ctx *ctx, const uint64_t *d_pages, uint32_t n, int32_t *d_codes,
+                       void *stream);
+
+/* Copy the cache tags to host: tag word per line (page << 20 | pin << 4 | ref << 2 |
+ * state).  out must hold agile_cache_lines(ctx) words.  Synchronises the device. */
+AGILE_API int agile_cache_tags(agile_ctx *ctx, uint64_t *host_out);
+AGILE_API uint64_t agile_cache_lines(agile_ctx *ctx);
+AGILE_API uint32_t agile_cache_sets(agile_ctx *ctx);
+
+/* Counters since init or the last reset (synchronises the device). */
+AGILE_API int agile_stats(agile_ctx *ctx, agile_stats_t *out);
+AGILE_API int agile_reset_stats(agile_ctx *ctx);
+
+/* Synchronise the device and return the first error recorded on the GPU since the
+ * last agile_check (0 if none), clearing it. */
+AGILE_API int agile_check(agile_ctx *ctx);
+
+/* Grid used by the library's kernels: CTAs per launch and threads per CTA. */
+AGILE_API int agile_launch_shape(agile_ctx *ctx, uint32_t *ctas, uint32_t *threads);
+
+AGILE_API const char *agile_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AGILE_H */

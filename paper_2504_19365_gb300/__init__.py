@@ -1,0 +1,256 @@
+"""Thin Python binding of the C-ABI in ``include/agile.h`` (argument marshalling only).
+
+Every function keeps the C name and takes plain integers for device pointers
+(``tensor.data_ptr()``) and streams (``torch.cuda.current_stream().cuda_stream``).
+All work runs in the CUDA library ``libagile.so``; there is no fallback: importing
+the binding without the built library raises at the first call.
+
+Paper: "AGILE: Lightweight and Efficient Asynchronous GPU-SSD Integration"
+(arXiv 2504.19365), Sec. 3 (design) and Sec. 4 (evaluation workloads).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libagile.so")
+
+PAGE_SIZE = 4096
+AGILE_OK = 0
+AGILE_EIO = -5
+AGILE_EAGAIN = -11
+AGILE_ENOMEM = -12
+AGILE_ENODEV = -19
+AGILE_EINVAL = -22
+AGILE_ETIMEDOUT = -110
+AGILE_ECUDA = -1000
+AGILE_SYNC = 0
+AGILE_ASYNC = 1
+AGILE_FAULT_EIO = 1
+AGILE_FAULT_DROP_CQE = 2
+AGILE_TOKEN_HIT = (1 << 64) - 1
+
+EXPORTED = [
+    "agile_config_default", "agile_init", "agile_destroy", "agile_store_write",
+    "agile_store_read", "agile_read_async", "agile_write_async", "agile_wait",
+    "agile_prefetch", "agile_flush", "agile_invalidate", "agile_embedding_bag", "agile_bfs",
+    "agile_cache_replay", "agile_cache_tags", "agile_cache_lines", "agile_cache_sets",
+    "agile_stats", "agile_reset_stats", "agile_check", "agile_launch_shape", "agile_strerror",
+]
+
+
+class agile_config(C.Structure):
+    _fields_ = [
+        ("store_bytes", C.c_uint64),
+        ("nvme_path", C.c_char_p),
+        ("cache_bytes", C.c_uint64),
+        ("ways", C.c_uint32),
+        ("num_queues", C.c_uint32),
+        ("queue_depth", C.c_uint32),
+        ("emu_latency_ns", C.c_uint32),
+        ("emu_queue_gbps", C.c_double),
+        ("wait_timeout_ns", C.c_uint64),
+        ("device", C.c_int32),
+        ("fault_flags", C.c_uint32),
+        ("fault_rate", C.c_double),
+        ("seed", C.c_uint64),
+        ("max_ctas", C.c_uint32),
+        ("prefetch_depth", C.c_uint32),
+    ]
+
+
+STAT_FIELDS = [
+    "hits", "misses", "busy_hits", "warp_coalesced", "share_retries", "evictions",
+    "writebacks", "eagain", "sq_full", "doorbells", "commands", "cqes", "cq_doorbells",
+    "io_errors", "bytes_read", "bytes_written", "prefetches", "timeouts",
+]
+
+
+class agile_stats_t(C.Structure):
+    _fields_ = [(f, C.c_uint64) for f in STAT_FIELDS]
+
+
+class AgileError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {code} ({strerror(code)})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load ``libagile.so``; raise if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build the CUDA library first "
+                "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = C.CDLL(LIB_PATH)
+        vp, u64, u32, i32 = C.c_void_p, C.c_uint64, C.c_uint32, C.c_int32
+        cfgp = C.POINTER(agile_config)
+        sig = {
+            "agile_config_default": (None, [cfgp]),
+            "agile_init": (C.c_int, [cfgp, C.POINTER(vp)]),
+            "agile_destroy": (C.c_int, [vp]),
+            "agile_store_write": (C.c_int, [vp, u64, vp, u64]),
+            "agile_store_read": (C.c_int, [vp, u64, vp, u64]),
+            "agile_read_async": (C.c_int, [vp, vp, u32, vp, vp, u32, vp]),
+            "agile_write_async": (C.c_int, [vp, vp, u32, vp, vp, vp]),
+            "agile_wait": (C.c_int, [vp, vp, u32, vp, vp]),
+            "agile_prefetch": (C.c_int, [vp, vp, u32, vp]),
+            "agile_flush": (C.c_int, [vp, vp]),
+            "agile_invalidate": (C.c_int, [vp, vp]),
+            "agile_embedding_bag": (C.c_int, [vp, u64, u32, u32, vp, vp, u32, vp, u32, vp]),
+            "agile_bfs": (C.c_int, [vp, u64, u64, u32, i32, vp, vp, u32, vp]),
+            "agile_cache_replay": (C.c_int, [vp, vp, u32, vp, vp]),
+            "agile_cache_tags": (C.c_int, [vp, vp]),
+            "agile_cache_lines": (u64, [vp]),
+            "agile_cache_sets": (u32, [vp]),
+            "agile_stats": (C.c_int, [vp, C.POINTER(agile_stats_t)]),
+            "agile_reset_stats": (C.c_int, [vp]),
+            "agile_check": (C.c_int, [vp]),
+            "agile_launch_shape": (C.c_int, [vp, C.POINTER(u32), C.POINTER(u32)]),
+            "agile_strerror": (C.c_char_p, [C.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().agile_strerror(int(code)).decode()
+    except Exception:
+        return "?"
+
+
+def _ok(code: int, what: str) -> int:
+    if code != 0:
+        raise AgileError(code, what)
+    return code
+
+
+# ----------------------------------------------------------------------------- C names
+
+def agile_config_default(**overrides) -> agile_config:
+    cfg = agile_config()
+    lib().agile_config_default(C.byref(cfg))
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def agile_init(cfg: agile_config) -> int:
+    h = C.c_void_p()
+    _ok(lib().agile_init(C.byref(cfg), C.byref(h)), "agile_init")
+    return h.value
+
+
+def agile_destroy(ctx: int) -> int:
+    return _ok(lib().agile_destroy(ctx), "agile_destroy")
+
+
+def agile_store_write(ctx: int, off: int, host_ptr: int, n: int) -> int:
+    return _ok(lib().agile_store_write(ctx, off, host_ptr, n), "agile_store_write")
+
+
+def agile_store_read(ctx: int, off: int, host_ptr: int, n: int) -> int:
+    return _ok(lib().agile_store_read(ctx, off, host_ptr, n), "agile_store_read")
+
+
+def agile_read_async(ctx, d_pages, n, d_dst, d_tok, mode, stream) -> int:
+    return _ok(lib().agile_read_async(ctx, d_pages, n, d_dst, d_tok, mode, stream), "agile_read_async")
+
+
+def agile_write_async(ctx, d_pages, n, d_src, d_tok, stream) -> int:
+    return _ok(lib().agile_write_async(ctx, d_pages, n, d_src, d_tok, stream), "agile_write_async")
+
+
+def agile_wait(ctx, d_tok, n, d_status, stream) -> int:
+    return _ok(lib().agile_wait(ctx, d_tok, n, d_status, stream), "agile_wait")
+
+
+def agile_prefetch(ctx, d_pages, n, stream) -> int:
+    return _ok(lib().agile_prefetch(ctx, d_pages, n, stream), "agile_prefetch")
+
+
+def agile_flush(ctx, stream) -> int:
+    return _ok(lib().agile_flush(ctx, stream), "agile_flush")
+
+
+def agile_invalidate(ctx, stream) -> int:
+    return _ok(lib().agile_invalidate(ctx, stream), "agile_invalidate")
+
+
+def agile_embedding_bag(ctx, table_byte0, rows, dim, d_idx, d_offsets, n_bags, d_out, mode, stream) -> int:
+    return _ok(lib().agile_embedding_bag(ctx, table_byte0, rows, dim, d_idx, d_offsets, n_bags, d_out,
+                                         mode, stream), "agile_embedding_bag")
+
+
+def agile_bfs(ctx, offsets_byte0, cols_byte0, n_vertices, src, d_level, d_edges, mode, stream) -> int:
+    return _ok(lib().agile_bfs(ctx, offsets_byte0, cols_byte0, n_vertices, src, d_level, d_edges, mode,
+                               stream), "agile_bfs")
+
+
+def agile_cache_replay(ctx, d_pages, n, d_codes, stream) -> int:
+    return _ok(lib().agile_cache_replay(ctx, d_pages, n, d_codes, stream), "agile_cache_replay")
+
+
+def agile_cache_tags(ctx, host_ptr) -> int:
+    return _ok(lib().agile_cache_tags(ctx, host_ptr), "agile_cache_tags")
+
+
+def agile_cache_lines(ctx) -> int:
+    return int(lib().agile_cache_lines(ctx))
+
+
+def agile_cache_sets(ctx) -> int:
+    return int(lib().agile_cache_sets(ctx))
+
+
+def agile_stats(ctx) -> dict:
+    s = agile_stats_t()
+    _ok(lib().agile_stats(ctx, C.byref(s)), "agile_stats")
+    return {f: int(getattr(s, f)) for f in STAT_FIELDS}
+
+
+def agile_reset_stats(ctx) -> int:
+    return _ok(lib().agile_reset_stats(ctx), "agile_reset_stats")
+
+
+def agile_check(ctx) -> int:
+    """Device-side error since the last check (0 if none); does not raise."""
+    return int(lib().agile_check(ctx))
+
+
+def agile_launch_shape(ctx):
+    a, b = C.c_uint32(), C.c_uint32()
+    _ok(lib().agile_launch_shape(ctx, C.byref(a), C.byref(b)), "agile_launch_shape")
+    return a.value, b.value
+
+
+def agile_strerror(code: int) -> str:
+    return strerror(code)
+
+
+# ----------------------------------------------------------------------------- tag word
+TAG_STATE_MASK = 3
+INVALID, BUSY, READY, MODIFIED = 0, 1, 2, 3
+
+
+def tag_page(t: int) -> int:
+    return int(t) >> 20
+
+
+def tag_state(t: int) -> int:
+    return int(t) & 3
+
+
+def tag_pins(t: int) -> int:
+    return (int(t) >> 4) & 0xFFFF

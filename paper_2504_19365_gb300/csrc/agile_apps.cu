@@ -1,0 +1,303 @@
+// Application drivers on top of the cache and queues: sum-pooled embedding bag
+// (Sec. 4.4, DLRM embedding lookups) and top-down level-synchronous BFS over CSR
+// (Sec. 4.5), each in a synchronous and an asynchronous mode.
+#include <cuda_runtime.h>
+
+#include "agile.h"
+#include "agile_ctx.cuh"
+#include "agile_dev.cuh"
+
+using namespace agile;
+
+namespace {
+
+constexpr int kMaxF4 = 8;  // float4 columns per lane: dim <= 32 * 4 * 8 = 1024
+
+// ============================================================================ embedding bag
+// out[b, :] = sum_{i in [off[b], off[b+1])} T[idx[i], :], FP32, indices in increasing i.
+//
+// One warp per bag; lane l accumulates the float4 columns l, l+32, ...  Rows are read
+// from the cache line with the line pinned for that one row only, so no pin is ever
+// held across a wait (Sec. 2.3.2).
+//   SYNC : each row's page is requested when the row is needed; a miss stalls the warp
+//          until it is filled (issue then stall, Sec. 4.4 "AGILE sync").
+//   ASYNC: pages are requested a group ahead (the next 32 indices of this bag, or the
+//          first 32 of the warp's next bag): the warp issues them, continues with the
+//          rows of the current group and only waits if a row's page is still in flight
+//          when it gets there (Sec. 4.4 "AGILE async": prefetch the next epoch).
+struct EmbApp {
+  uint64_t page0;  // first store page of the table
+  uint32_t rows, dim;
+  const int64_t *idx;
+  const int64_t *off;
+  uint32_t n_bags;
+  float *out;
+  uint32_t mode;
+
+  __device__ __forceinline__ uint64_t row_page(uint64_t r) const { return page0 + (r * dim * 4) / kPage; }
+
+  // issue (without waiting) the pages of indices [i0, min(i0+32, e))
+  __device__ bool prefetch_group(const Dev &d, const AppCtx &a, int64_t i0, int64_t e) const {
+    unsigned l = lane_id();
+    int64_t i = i0 + l;
+    bool want = i < e;
+    uint64_t r = want ? (uint64_t)idx[i] : 0;
+    if (want && r >= rows) {
+      set_error(d, AGILE_EINVAL);
+      want = false;
+    }
+    return warp_request(d, want, row_page(r), a.q0, false, a.deadline);
+  }
+
+  __device__ void run(const Dev &d, const AppCtx &a) const {
+    unsigned l = lane_id();
+    const uint32_t nf4 = dim / 4;
+    const bool async = mode == AGILE_ASYNC;
+    uint32_t b = a.warp;
+    if (b >= n_bags) return;
+    int64_t s = off[b], e = off[b + 1];
+    if (async && s < e && !prefetch_group(d, a, s, e)) return;
+    for (; b < n_bags; b += a.n_warps) {
+      s = off[b];
+      e = off[b + 1];
+      float4 acc[kMaxF4];
+#pragma unroll
+      for (int k = 0; k < kMaxF4; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int64_t i0 = s; i0 < e; i0 += 32) {
+        // lookahead: the next group of this bag, else the first group of the next bag
+        if (async) {
+          if (i0 + 32 < e) {
+            if (!prefetch_group(d, a, i0 + 32, e)) return;
+          } else {
+            uint64_t nb = (uint64_t)b + a.n_warps;
+            if (nb < n_bags) {
+              int64_t ns = off[nb], ne = off[nb + 1];
+              if (ns < ne && !prefetch_group(d, a, ns, ne)) return;
+            }
+          }
+        }
+        int64_t i = i0 + l;
+        uint64_t r = i < e ? (uint64_t)idx[i] : 0;
+        if (i < e && r >= rows) {
+          set_error(d, AGILE_EINVAL);
+          r = 0;
+        }
+        uint32_t cnt = (uint32_t)min((int64_t)32, e - i0);
+        for (uint32_t j = 0; j < cnt; ++j) {
+          uint64_t rj = __shfl_sync(kFull, r, j);
+          uint64_t byte = rj * dim * 4;
+          uint64_t pg = page0 + byte / kPage;
+          uint32_t inpage = (uint32_t)(byte % kPage);
+          uint32_t line;
+          if (!warp_pin_page(d, pg, a.q0, a.deadline, line)) return;
+          const uint8_t *rowp = line_ptr(d, line) + inpage;
+#pragma unroll
+          for (int k = 0; k < kMaxF4; ++k) {
+            uint32_t c = l + 32 * k;
+            if (c < nf4) {
+              float4 v = ld_cg_f4(rowp + 16 * c);
+              acc[k].x = __fadd_rn(acc[k].x, v.x);
+              acc[k].y = __fadd_rn(acc[k].y, v.y);
+              acc[k].z = __fadd_rn(acc[k].z, v.z);
+              acc[k].w = __fadd_rn(acc[k].w, v.w);
+            }
+          }
+          __syncwarp();
+          if (l == 0) cache_unpin(d, line);
+        }
+      }
+      float4 *o = (float4 *)(out + (uint64_t)b * dim);
+#pragma unroll
+      for (int k = 0; k < kMaxF4; ++k) {
+        uint32_t c = l + 32 * k;
+        if (c < nf4) o[c] = acc[k];
+      }
+    }
+  }
+};
+
+// ============================================================================ BFS
+// Level-synchronous top-down BFS (Sec. 4.5 BFS over CSR, through the cache).
+// Level L: app warps claim chunks of 128 consecutive vertex ids; a lane owns one
+// vertex and takes part when level[v] == L.  Its offsets[v], offsets[v+1] (int64) and
+// its neighbour list (int32) are read through the cache; every neighbour u with
+// level[u] == -1 gets level L+1 by compare-and-swap.  Vertices are visited in id order,
+// so neighbouring lists that share a page are read while the page is resident.  A grid
+// barrier over the app warps ends each level; the search stops when a level discovers
+// nothing.  Edges scanned = sum of the degrees of the frontier vertices of all levels.
+//   SYNC : each page (offsets, columns) is requested when needed and waited for.
+//   ASYNC: before scanning a chunk, all column pages of its frontier vertices are
+//          issued at once; offsets pages of the next chunk are issued ahead.
+struct BfsApp {
+  uint64_t off_page0, col_page0;
+  uint32_t n;
+  int32_t *level;
+  unsigned long long *edges_out;
+  uint32_t mode;
+
+  static constexpr uint32_t kChunk = 128;
+
+  // read an int64 (offsets) or int32 (columns) element at byte `byte` of the array
+  // starting at store page `page0`, for lanes with `want`, through the cache: the warp
+  // walks the distinct pages of the requests, pinning each one for its reads only.
+  template <typename T>
+  __device__ bool gather(const Dev &d, const AppCtx &a, uint64_t page0, bool want, uint64_t byte, T &val) const {
+    uint64_t pg = page0 + byte / kPage;
+    uint32_t in = (uint32_t)(byte % kPage);
+    bool todo = want;
+    while (__any_sync(kFull, todo)) {
+      unsigned m = __ballot_sync(kFull, todo);
+      uint64_t p = __shfl_sync(kFull, pg, __ffs(m) - 1);
+      uint32_t line;
+      if (!warp_pin_page(d, p, a.q0, a.deadline, line)) return false;
+      if (todo && pg == p) {
+        const uint8_t *src = line_ptr(d, line) + in;
+        if (sizeof(T) == 8) val = (T)ld_cg_s64(src);
+        else val = (T)ld_cg_s32(src);
+        todo = false;
+      }
+      __syncwarp();
+      if (lane_id() == 0) cache_unpin(d, line);
+    }
+    return true;
+  }
+
+  __device__ bool chunk(const Dev &d, const AppCtx &a, uint32_t v0, int32_t L, uint32_t &found,
+                        unsigned long long &scanned) const {
+    unsigned l = lane_id();
+    uint32_t v = v0 + l;
+    bool f = v < n && ld_rlx32((const uint32_t *)&level[v]) == (uint32_t)L;
+    if (!__any_sync(kFull, f)) return true;
+    const bool async = mode == AGILE_ASYNC;
+    // offsets[v], offsets[v+1]
+    if (async) {
+      if (!warp_request(d, f, off_page0 + ((uint64_t)v * 8) / kPage, a.q0, false, a.deadline)) return false;
+      if (!warp_request(d, f, off_page0 + ((uint64_t)v * 8 + 8) / kPage, a.q0, false, a.deadline)) return false;
+    }
+    int64_t s = 0, e = 0;
+    if (!gather<int64_t>(d, a, off_page0, f, (uint64_t)v * 8, s)) return false;
+    if (!gather<int64_t>(d, a, off_page0, f, (uint64_t)v * 8 + 8, e)) return false;
+    uint32_t deg = f ? (uint32_t)(e - s) : 0;
+    // exclusive prefix of the degrees over the warp
+    uint32_t incl = deg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(kFull, incl, o);
+      if (l >= (unsigned)o) incl += t;
+    }
+    uint32_t excl = incl - deg;
+    uint32_t total = __shfl_sync(kFull, incl, 31);
+    scanned += total;
+    if (total == 0) return true;
+    if (async) {
+      // issue every column page of the chunk's frontier lists, page by page per lane
+      uint64_t cp0 = col_page0 + ((uint64_t)s * 4) / kPage;
+      uint64_t cp1 = deg ? col_page0 + ((uint64_t)(e - 1) * 4) / kPage : cp0;
+      for (uint64_t k = 0;; ++k) {
+        bool want = deg && cp0 + k <= cp1;
+        if (!__any_sync(kFull, want)) break;
+        if (!warp_request(d, want, cp0 + k, a.q0, false, a.deadline)) return false;
+        if (k >= 64) break;  // very long lists are fetched on demand past this point
+      }
+    }
+    for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+      uint32_t k = k0 + l;
+      bool act = k < total;
+      // owner lane j: the last lane whose exclusive prefix is <= k
+      uint32_t j = 0;
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        uint32_t cand = j + step;
+        uint32_t ex = __shfl_sync(kFull, excl, cand & 31);
+        if (cand < 32 && ex <= k) j = cand;
+      }
+      int64_t sj = __shfl_sync(kFull, s, j);
+      uint32_t exj = __shfl_sync(kFull, excl, j);
+      uint64_t pos = (uint64_t)sj + (k - exj);
+      int32_t u = 0;
+      if (!gather<int32_t>(d, a, col_page0, act, pos * 4, u)) return false;
+      if (act && (uint32_t)u < n) {
+        if (ld_rlx32((const uint32_t *)&level[u]) == 0xFFFFFFFFu &&
+            atomicCAS((int *)&level[u], -1, L + 1) == -1)
+          found++;
+      }
+    }
+    return true;
+  }
+
+  __device__ void run(const Dev &d, const AppCtx &a) const {
+    unsigned l = lane_id();
+    uint32_t nchunks = (n + kChunk - 1) / kChunk;
+    unsigned long long scanned = 0;
+    for (int32_t L = 0;; ++L) {
+      if (a.warp == 0 && l == 0) {
+        // the chunk counter of level L+1 was last used at level L-1, whose chunks were
+        // all claimed before barrier L-1; the discovery counter of level L+1 (three
+        // slots) was last read right after barrier L-2, which every warp has left
+        st_rlx32(&d.run->work[(L + 1) & 1], 0u);
+        st_rlx64(&d.run->acc[1 + (L + 1) % 3], 0ull);
+      }
+      uint32_t found = 0;
+      for (;;) {
+        uint32_t c = 0;
+        if (l == 0) c = atomicAdd(&d.run->work[L & 1], 1u);
+        c = __shfl_sync(kFull, c, 0);
+        if (c >= nchunks || aborted(d)) break;
+        for (uint32_t sub = 0; sub < kChunk; sub += 32)
+          if (!chunk(d, a, c * kChunk + sub, L, found, scanned)) break;
+      }
+      uint32_t tot = __reduce_add_sync(kFull, found);
+      if (l == 0 && tot) atomicAdd(&d.run->acc[1 + L % 3], (unsigned long long)tot);
+      if (!app_barrier(d, a.n_warps, a.deadline)) return;
+      if (aborted(d)) return;
+      uint64_t disc = ld_acq64(&d.run->acc[1 + L % 3]);
+      if (disc == 0) break;
+    }
+    if (l == 0 && scanned) atomicAdd(&d.run->acc[0], scanned);
+    if (!app_barrier(d, a.n_warps, a.deadline)) return;
+    if (a.warp == 0 && l == 0 && edges_out) *edges_out = ld_acq64(&d.run->acc[0]);
+  }
+};
+
+__global__ void bfs_init_kernel(int32_t *level, uint32_t n, int32_t src) {
+  uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i < n) level[i] = (i == (uint64_t)src) ? 0 : -1;
+}
+
+}  // namespace
+
+extern "C" {
+
+int agile_embedding_bag(agile_ctx *c, uint64_t table_byte0, uint32_t rows, uint32_t dim, const int64_t *d_idx,
+                        const int64_t *d_offsets, uint32_t n_bags, float *d_out, uint32_t mode, void *stream) {
+  if (!c || mode > 1) return AGILE_EINVAL;
+  if (n_bags == 0) return AGILE_OK;
+  if (!d_idx || !d_offsets || !d_out) return AGILE_EINVAL;
+  if (dim == 0 || dim % 4 || dim * 4 > kPage || dim > 32 * 4 * kMaxF4) return AGILE_EINVAL;
+  if (table_byte0 % kPage) return AGILE_EINVAL;
+  if (table_byte0 + (uint64_t)rows * dim * 4 > c->cfg.store_bytes) return AGILE_EINVAL;
+  if (((uintptr_t)d_out) & 15) return AGILE_EINVAL;
+  // rows must not straddle pages: dim*4 divides the page
+  if (kPage % (dim * 4)) return AGILE_EINVAL;
+  EmbApp app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, mode};
+  return launch_engine(c, app, stream);
+}
+
+int agile_bfs(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_t n_vertices, int32_t src,
+              int32_t *d_level, uint64_t *d_edges_scanned, uint32_t mode, void *stream) {
+  if (!c || mode > 1 || !d_level) return AGILE_EINVAL;
+  if (offsets_byte0 % kPage || cols_byte0 % kPage) return AGILE_EINVAL;
+  if (n_vertices == 0 || src < 0 || (uint32_t)src >= n_vertices) return AGILE_EINVAL;
+  if (offsets_byte0 + ((uint64_t)n_vertices + 1) * 8 > c->cfg.store_bytes) return AGILE_EINVAL;
+  if (cols_byte0 >= c->cfg.store_bytes) return AGILE_EINVAL;
+  AGILE_CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t s = as_stream(stream);
+  bfs_init_kernel<<<(n_vertices + 255) / 256, 256, 0, s>>>(d_level, n_vertices, src);
+  AGILE_CUDA_TRY(cudaGetLastError());
+  if (d_edges_scanned) AGILE_CUDA_TRY(cudaMemsetAsync(d_edges_scanned, 0, 8, s));
+  BfsApp app{offsets_byte0 / kPage, cols_byte0 / kPage, n_vertices, d_level,
+             (unsigned long long *)d_edges_scanned, mode};
+  return launch_engine(c, app, stream);
+}
+
+}  // extern "C"

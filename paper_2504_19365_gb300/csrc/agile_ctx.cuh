@@ -1,0 +1,66 @@
+// Host-side context of the library and the launcher of the engine kernel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <vector>
+
+#include "agile.h"
+#include "agile_dev.cuh"
+
+struct agile_ctx {
+  agile_config cfg;
+  int device = 0;
+  int sms = 0;
+  agile::Dev dev{};
+  void *store_host = nullptr;
+  std::vector<void *> dallocs;
+  int last_cuda_error = 0;
+};
+
+namespace agile {
+
+#define AGILE_CUDA_TRY(expr)                                                         \
+  do {                                                                               \
+    cudaError_t e__ = (expr);                                                        \
+    if (e__ != cudaSuccess) {                                                        \
+      fprintf(stderr, "agile: %s failed: %s\n", #expr, cudaGetErrorString(e__));     \
+      return AGILE_ECUDA;                                                            \
+    }                                                                                \
+  } while (0)
+
+inline cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
+
+// Largest co-resident grid for this engine instantiation (cooperative launch rule:
+// every CTA must be resident at once, because the service warps and the waiting app
+// warps of one launch depend on each other).
+template <class App>
+int engine_grid(agile_ctx *c) {
+  static int per_sm = -1;  // one value per instantiation
+  if (per_sm < 0) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, engine_kernel<App>, kThreads, 0) != cudaSuccess)
+      return 0;
+    per_sm = n;
+  }
+  int g = per_sm * c->sms;
+  if (c->cfg.max_ctas && (int)c->cfg.max_ctas < g) g = (int)c->cfg.max_ctas;
+  return g;
+}
+
+template <class App>
+int launch_engine(agile_ctx *c, const App &app, void *stream, int grid_override = 0) {
+  cudaStream_t s = as_stream(stream);
+  AGILE_CUDA_TRY(cudaSetDevice(c->device));
+  int grid = grid_override > 0 ? grid_override : engine_grid<App>(c);
+  if (grid <= 0) return AGILE_ECUDA;
+  AGILE_CUDA_TRY(cudaMemsetAsync(c->dev.run, 0, sizeof(RunState), s));
+  Dev d = c->dev;
+  App a = app;
+  void *args[] = {(void *)&d, (void *)&a};
+  AGILE_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)engine_kernel<App>, dim3(grid), dim3(kThreads),
+                                             args, 0, s));
+  return AGILE_OK;
+}
+
+}  // namespace agile

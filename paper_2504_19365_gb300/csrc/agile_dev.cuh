@@ -1,0 +1,951 @@
+// Device-side state and primitives of the AGILE I/O path for sm_103a.
+//
+// Layout in HBM (all library-owned, allocated once per context):
+//   lines      [nlines * 4096]      cache data, one 4 KiB line per store page (Sec. 2.3.3)
+//   tag        [nlines] u64         {page:44 | pin:16 | wb:1 | ref:1 | state:2} (Sec. 3.4)
+//   hand       [sets]   u32         clock hand per set (Sec. 4.4, clock policy)
+//   sh_key/val [buckets*4] u64      in-flight share table, 4 slots per bucket (Sec. 3.4.1)
+//   sq         [Q * depth] 64 B     NVMe submission entries (Sec. 2.1)
+//   cq         [Q * depth] 16 B     NVMe completion entries with phase bit (Sec. 2.1)
+//   sqe_state  [Q * depth] u64      {ticket:62 | EMPTY/UPDATED/ISSUED} (Sec. 3.3.1)
+//   cmd_ctx    [Q * depth] u64      what a completion releases (line fill, write-back)
+//   cmpl       [Q * depth] u64      completion word = transaction barrier (Sec. 3.2.1)
+//   sq_resv    [Q] u64              {in flight:32 | next ticket:32}
+//   sq_tail/sq_lock/sq_db [Q] u32   doorbell-lock holder's tail, the lock, doorbell
+//   cq_db      [Q] u32              CQ head doorbell
+//   cq_poll    [Q*4] u32            Alg. 1 state {offset, mask, phase}
+//   emu*                            emulated device: fetch head, CQ tail, phase, timing
+//   staging    [Q * depth * 4096]   write-back sources, one page per submission slot
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace agile {
+
+constexpr uint32_t kPage = 4096;
+constexpr int kWarps = 8;             // warps per CTA: warp 0 = service, 1..7 = app
+constexpr int kThreads = kWarps * 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------- tag word (Sec. 3.4)
+constexpr uint64_t ST_MASK = 3, ST_INVALID = 0, ST_BUSY = 1, ST_READY = 2, ST_MODIFIED = 3;
+constexpr uint64_t TAG_REF = 1ull << 2;
+constexpr uint64_t TAG_WB = 1ull << 3;
+constexpr int PIN_SHIFT = 4;
+constexpr uint64_t PIN1 = 1ull << PIN_SHIFT;
+constexpr uint64_t PIN_MASK = 0xFFFFull << PIN_SHIFT;
+constexpr int PAGE_SHIFT = 20;
+__host__ __device__ __forceinline__ uint64_t tag_page(uint64_t t) { return t >> PAGE_SHIFT; }
+__host__ __device__ __forceinline__ uint64_t tag_state(uint64_t t) { return t & ST_MASK; }
+__host__ __device__ __forceinline__ uint64_t tag_make(uint64_t page, uint64_t st, bool ref) {
+  return (page << PAGE_SHIFT) | (ref ? TAG_REF : 0) | st;
+}
+
+// ---------------------------------------------------------------- queues (Sec. 3.3.1)
+constexpr uint64_t SQE_EMPTY = 0, SQE_UPDATED = 1, SQE_ISSUED = 2;
+constexpr uint32_t OP_FLUSH = 0x00, OP_WRITE = 0x01, OP_READ = 0x02;
+
+// command context: what the completion of a command releases
+constexpr uint64_t CTX_NOP = 0, CTX_FILL = 1, CTX_WB = 2;
+__host__ __device__ __forceinline__ uint64_t ctx_make(uint64_t kind, uint32_t share_slot, uint32_t idx) {
+  return (kind << 60) | ((uint64_t)(share_slot & 0x0FFFFFFFu) << 32) | idx;
+}
+
+struct alignas(64) Sqe { uint32_t dw[16]; };
+struct alignas(16) Cqe { uint32_t dw[4]; };
+
+// statistic slots (mirror agile_stats_t order)
+enum Stat {
+  S_HITS, S_MISSES, S_BUSY_HITS, S_WARP_COALESCED, S_SHARE_RETRIES, S_EVICTIONS, S_WRITEBACKS,
+  S_EAGAIN, S_SQ_FULL, S_DOORBELLS, S_COMMANDS, S_CQES, S_CQ_DOORBELLS, S_IO_ERRORS,
+  S_BYTES_READ, S_BYTES_WRITTEN, S_PREFETCHES, S_TIMEOUTS, S_COUNT
+};
+
+// per-launch state, zeroed before every launch
+struct RunState {
+  uint32_t app_done;      // app warps finished
+  uint32_t error;         // first error code (negated AGILE_E*), 0 = none
+  uint32_t bar_count;     // grid barrier arrivals
+  uint32_t bar_gen;       // grid barrier generation
+  uint32_t work[4];       // dynamic work counters
+  unsigned long long acc[4];  // accumulators (edges scanned, discovered vertices, ...)
+  uint32_t flag[4];
+};
+
+struct Dev {
+  // backing store (pinned host memory, device-visible address)
+  uint8_t *store;
+  uint64_t store_bytes;
+  // cache
+  uint8_t *lines;
+  unsigned long long *tag;
+  uint32_t *hand;
+  uint64_t nlines;
+  uint32_t sets, ways;
+  unsigned long long *sh_key;
+  unsigned long long *sh_val;
+  uint32_t sh_mask;  // buckets - 1 (power of two)
+  // queues
+  uint32_t Q, depth, dmask, dlog;
+  Sqe *sq;
+  Cqe *cq;
+  unsigned long long *sqe_state;
+  unsigned long long *cmd_ctx;
+  unsigned long long *cmpl;
+  unsigned long long *sq_resv;
+  uint32_t *sq_tail, *sq_lock, *sq_db, *cq_db, *cq_poll;
+  uint32_t *emu;  // [Q*4] {sq_head, cq_tail, cq_phase, seen}
+  unsigned long long *emu_busy;     // [Q] ns at which the queue's device pipe is free
+  unsigned long long *emu_arrival;  // [Q*depth] ns at which the device saw the command
+  uint8_t *staging;
+  // emulated device model
+  uint64_t lat_ns, ns_per_page;
+  uint32_t fault_flags, fault_thresh;
+  uint64_t seed;
+  // run
+  RunState *run;
+  unsigned long long *stats;
+  uint64_t timeout_ns;
+  uint32_t prefetch_depth;
+  int32_t *err_sticky;  // first error since the last agile_check
+};
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ uint32_t ld_acq32(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t ld_acq64(const unsigned long long *p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_rlx32(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t ld_rlx64(const unsigned long long *p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rel32(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_rel64(unsigned long long *p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_rlx64(unsigned long long *p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_rlx32(uint32_t *p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_sc() { asm volatile("fence.sc.gpu;" ::: "memory"); }
+__device__ __forceinline__ void fence_ar() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+// 16-byte loads/stores that bypass L1: cache lines and store pages are rewritten by
+// other SMs during a launch, so nothing here may be served from a stale L1 copy.
+__device__ __forceinline__ int4 ld_cg16(const void *p) {
+  int4 v;
+  asm volatile("ld.global.cg.v4.s32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_cg16(void *p, int4 v) {
+  asm volatile("st.global.cg.v4.s32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
+               "r"(v.w) : "memory");
+}
+__device__ __forceinline__ float4 ld_cg_f4(const void *p) {
+  int4 v = ld_cg16(p);
+  return make_float4(__int_as_float(v.x), __int_as_float(v.y), __int_as_float(v.z), __int_as_float(v.w));
+}
+__device__ __forceinline__ int32_t ld_cg_s32(const void *p) {
+  int32_t v;
+  asm volatile("ld.global.cg.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int64_t ld_cg_s64(const void *p) {
+  int64_t v;
+  asm volatile("ld.global.cg.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ void stat_add(const Dev &d, int s, uint64_t v) {
+  if (v) atomicAdd(&d.stats[s], (unsigned long long)v);
+}
+// warp-aggregated statistic: every lane passes its own count
+__device__ __forceinline__ void stat_warp(const Dev &d, int s, uint32_t v) {
+  unsigned b = __ballot_sync(kFull, v != 0);
+  if (!b) return;
+  uint32_t sum = __reduce_add_sync(kFull, v);
+  if (lane_id() == 0) atomicAdd(&d.stats[s], (unsigned long long)sum);
+}
+
+// record the first error of the launch and of the context
+__device__ __forceinline__ void set_error(const Dev &d, int code) {
+  atomicCAS(&d.run->error, 0u, (uint32_t)(-code));
+  atomicCAS((uint32_t *)d.err_sticky, 0u, (uint32_t)(-code));
+  if (code == -110) atomicAdd(&d.stats[S_TIMEOUTS], 1ull);
+}
+__device__ __forceinline__ bool aborted(const Dev &d) { return ld_rlx32(&d.run->error) != 0; }
+
+__device__ __forceinline__ void backoff(uint32_t &ns) {
+  __nanosleep(ns);
+  ns = ns < 2048 ? ns * 2 : 2048;
+}
+
+// ---------------------------------------------------------------- cache geometry
+// Set index: golden-ratio multiplicative hash of the page, upper 32 bits scaled to
+// [0, sets).  Works for any number of sets.
+__host__ __device__ __forceinline__ uint32_t set_of(uint64_t page, uint32_t sets) {
+  uint64_t h = page * 0x9E3779B97F4A7C15ull;
+  return (uint32_t)(((h >> 32) * (uint64_t)sets) >> 32);
+}
+__device__ __forceinline__ uint8_t *line_ptr(const Dev &d, uint64_t line) {
+  return d.lines + line * (uint64_t)kPage;
+}
+
+// ---------------------------------------------------------------- warp page copy
+// One warp moves one 4 KiB page with 16-byte accesses: 8 loads in flight per lane,
+// then 8 stores, so each request is a single 512-byte coalesced transaction per step.
+__device__ __forceinline__ void warp_copy_page(void *dst, const void *src) {
+  const int4 *s = (const int4 *)src;
+  int4 *t = (int4 *)dst;
+  unsigned l = lane_id();
+  int4 v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = ld_cg16(s + k * 32 + l);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) st_cg16(t + k * 32 + l, v[k]);
+}
+// A single thread moves a page (rare paths: write-back copies inside a lane's miss).
+__device__ __forceinline__ void lane_copy_page(void *dst, const void *src) {
+  const int4 *s = (const int4 *)src;
+  int4 *t = (int4 *)dst;
+  for (int k = 0; k < 256; k += 16) {
+    int4 v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = ld_cg16(s + k + j);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) st_cg16(t + k + j, v[j]);
+  }
+}
+
+// ================================================================ submission side
+// Alg. 2, check_full: reserve n consecutive slots of queue q.  A slot is free when
+// the command that used it last has completed (state EMPTY) and fewer than depth-1
+// commands are outstanding (the NVMe full rule).  Never waits.
+__device__ __forceinline__ bool sq_try_reserve(const Dev &d, uint32_t q, uint32_t n,
+                                               uint32_t &slot, uint32_t &ticket) {
+  unsigned long long *rp = &d.sq_resv[q];
+  uint64_t w = ld_rlx64(rp);
+  for (int tries = 0; tries < 4; ++tries) {
+    uint32_t t = (uint32_t)w, infl = (uint32_t)(w >> 32);
+    if (infl + n > d.depth - 1) return false;
+    for (uint32_t k = 0; k < n; ++k) {
+      uint64_t st = ld_acq64(&d.sqe_state[(uint64_t)q * d.depth + ((t + k) & d.dmask)]);
+      if ((st & 3) != SQE_EMPTY) return false;
+    }
+    uint64_t nw = ((uint64_t)(infl + n) << 32) | (uint32_t)(t + n);
+    uint64_t old = atomicCAS(rp, (unsigned long long)w, (unsigned long long)nw);
+    if (old == w) {
+      slot = t & d.dmask;
+      ticket = t;
+      return true;
+    }
+    w = old;
+  }
+  return false;
+}
+
+// SQ selection (Sec. 3.3.1): start at the thread's own queue, on a full queue try the
+// next one; false after one pass over every queue.
+__device__ __forceinline__ bool sq_reserve_any(const Dev &d, uint32_t q0, uint32_t n, uint32_t &q,
+                                               uint32_t &slot, uint32_t &ticket) {
+  for (uint32_t k = 0; k < d.Q; ++k) {
+    uint32_t qq = q0 + k;
+    if (qq >= d.Q) qq -= d.Q;
+    if (sq_try_reserve(d, qq, n, slot, ticket)) {
+      q = qq;
+      return true;
+    }
+  }
+  atomicAdd(&d.stats[S_SQ_FULL], 1ull);
+  return false;
+}
+
+// Alg. 2, enqueue_cmd + update_SQE: write the 64-byte command, then publish the slot
+// as UPDATED.  CID = slot index (unique while the command is outstanding).
+__device__ __forceinline__ void sq_commit(const Dev &d, uint32_t q, uint32_t slot, uint32_t ticket,
+                                          uint32_t opcode, uint64_t prp1, uint64_t page,
+                                          uint64_t ctx) {
+  uint64_t i = (uint64_t)q * d.depth + slot;
+  uint32_t *e = d.sq[i].dw;
+  uint64_t slba = page * (kPage / 512);
+  int4 a = make_int4((int)(opcode | (slot << 16)), 1, 0, 0);                      // dw0-3
+  int4 b = make_int4(0, 0, (int)(uint32_t)prp1, (int)(uint32_t)(prp1 >> 32));      // dw4-7
+  int4 c = make_int4(0, 0, (int)(uint32_t)slba, (int)(uint32_t)(slba >> 32));      // dw8-11
+  int4 f = make_int4((int)(kPage / 512 - 1), 0, 0, 0);                             // dw12-15
+  st_cg16(e, a);
+  st_cg16(e + 4, b);
+  st_cg16(e + 8, c);
+  st_cg16(e + 12, f);
+  st_rlx64(&d.cmd_ctx[i], ctx);
+  fence_ar();
+  st_rel64(&d.sqe_state[i], ((uint64_t)ticket << 2) | SQE_UPDATED);
+}
+
+// Alg. 2, move_SQ_tail: the doorbell-lock holder turns UPDATED slots into ISSUED from
+// the tail up to the first slot that is not UPDATED, then writes the doorbell once.
+__device__ __forceinline__ void sq_move_tail(const Dev &d, uint32_t q) {
+  uint32_t t = ld_rlx32(&d.sq_tail[q]);
+  uint32_t n = 0;
+  while (n < d.depth) {
+    uint64_t i = (uint64_t)q * d.depth + (t & d.dmask);
+    uint64_t st = ld_acq64(&d.sqe_state[i]);
+    if (st != (((uint64_t)t << 2) | SQE_UPDATED)) break;
+    st_rlx64(&d.sqe_state[i], ((uint64_t)t << 2) | SQE_ISSUED);
+    ++t;
+    ++n;
+  }
+  if (n) {
+    st_rlx32(&d.sq_tail[q], t);
+    fence_ar();
+    st_rel32(&d.sq_db[q], t & d.dmask);
+    atomicAdd(&d.stats[S_DOORBELLS], 1ull);
+  }
+}
+
+// Alg. 2, Attempt_SQDB: try the doorbell lock, move the tail if it is ours, and report
+// whether our command has left the UPDATED state.
+__device__ __forceinline__ bool sq_attempt_db(const Dev &d, uint32_t q, uint32_t slot, uint32_t ticket) {
+  if (atomicCAS(&d.sq_lock[q], 0u, 1u) == 0u) {
+    fence_ar();
+    sq_move_tail(d, q);
+    fence_ar();
+    atomicExch(&d.sq_lock[q], 0u);
+  }
+  uint64_t st = ld_acq64(&d.sqe_state[(uint64_t)q * d.depth + slot]);
+  return !((st >> 2) == (uint64_t)ticket && (st & 3) == SQE_UPDATED);
+}
+
+// Warp-collective doorbell batching: lanes with `has` committed a command to queue q.
+// One leader per queue rings for the whole group; then every lane repeats
+// Attempt_SQDB until its own command is ISSUED (bounded by the deadline).
+__device__ __forceinline__ bool warp_ring(const Dev &d, bool has, uint32_t q, uint32_t slot,
+                                          uint32_t ticket, uint64_t deadline) {
+  unsigned m = __match_any_sync(kFull, has ? q : 0xFFFFFFFFu);
+  bool leader = has && (__ffs(m) - 1 == (int)lane_id());
+  bool pending = has;
+  if (leader) pending = !sq_attempt_db(d, q, slot, ticket);
+  __syncwarp();
+  if (has && pending) {
+    uint64_t st = ld_acq64(&d.sqe_state[(uint64_t)q * d.depth + slot]);
+    pending = ((st >> 2) == (uint64_t)ticket && (st & 3) == SQE_UPDATED);
+  }
+  uint32_t ns = 32;
+  while (pending) {
+    if (sq_attempt_db(d, q, slot, ticket)) break;
+    if (gtimer() > deadline) {
+      set_error(d, -110);
+      return false;
+    }
+    backoff(ns);
+  }
+  return true;
+}
+
+// ================================================================ in-flight share table
+// Sec. 3.4.1: page -> request in flight.  A bucket of 4 slots per hash; the slot key is
+// page+1 (0 = free).  Inserting the key is how a thread takes ownership of a page's
+// miss (or write); any other thread that finds the key defers and retries.
+constexpr uint64_t SH_FILL = 1, SH_WRITE = 2;
+__device__ __forceinline__ uint32_t sh_bucket(const Dev &d, uint64_t page) {
+  uint64_t h = (page + 0x632BE59BD9B4E019ull) * 0xC2B2AE3D27D4EB4Full;
+  return (uint32_t)(h >> 40) & d.sh_mask;
+}
+// returns slot index >= 0 when inserted, -1 when the page is already present (or a
+// racing insert of the same page was seen), -2 when the bucket is full.
+__device__ __forceinline__ int64_t sh_insert(const Dev &d, uint64_t page, uint64_t kind) {
+  uint64_t key = page + 1;
+  uint64_t base = (uint64_t)sh_bucket(d, page) * 4;
+  for (int tries = 0; tries < 8; ++tries) {
+    int free_k = -1;
+    for (int k = 0; k < 4; ++k) {
+      uint64_t v = ld_acq64(&d.sh_key[base + k]);
+      if (v == key) return -1;
+      if (v == 0 && free_k < 0) free_k = k;
+    }
+    if (free_k < 0) return -2;
+    if (atomicCAS(&d.sh_key[base + free_k], 0ull, (unsigned long long)key) != 0ull) continue;
+    // a racing insert of the same key into another slot: whoever sees the other backs off
+    fence_sc();
+    bool dup = false;
+    for (int k = 0; k < 4; ++k)
+      if (k != free_k && ld_acq64(&d.sh_key[base + k]) == key) dup = true;
+    if (dup) {
+      st_rel64(&d.sh_key[base + free_k], 0ull);
+      return -1;
+    }
+    st_rlx64(&d.sh_val[base + free_k], kind);
+    return (int64_t)(base + free_k);
+  }
+  return -2;
+}
+__device__ __forceinline__ void sh_remove(const Dev &d, uint64_t slot) {
+  st_rlx64(&d.sh_val[slot], 0ull);
+  st_rel64(&d.sh_key[slot], 0ull);
+}
+
+// ================================================================ cache (Sec. 3.4)
+enum Probe { P_HIT = 0, P_BUSY = 1, P_MISS = 2 };
+
+// Look the page up in its set.  READY/MODIFIED -> hit (case a): the reference bit is
+// set and, with `pin`, the line is pinned against eviction.  BUSY -> in flight
+// (case c).  Otherwise a miss.
+__device__ __forceinline__ int cache_probe(const Dev &d, uint64_t page, bool pin, uint32_t &line) {
+  uint64_t base = (uint64_t)set_of(page, d.sets) * d.ways;
+  for (uint32_t w = 0; w < d.ways; ++w) {
+    uint64_t t = ld_rlx64(&d.tag[base + w]);
+    uint64_t st = tag_state(t);
+    if (st == ST_INVALID || tag_page(t) != page) continue;
+    line = (uint32_t)(base + w);
+    if (st == ST_BUSY) return P_BUSY;
+    if (!pin) {
+      if (!(t & TAG_REF)) atomicOr(&d.tag[base + w], TAG_REF);
+      return P_HIT;
+    }
+    uint64_t old = atomicAdd(&d.tag[base + w], PIN1);
+    uint64_t ost = tag_state(old);
+    if (tag_page(old) == page && (ost == ST_READY || ost == ST_MODIFIED)) {
+      if (!(old & TAG_REF)) atomicOr(&d.tag[base + w], TAG_REF);
+      fence_ar();  // the line data is read after the pin is observed
+      return P_HIT;
+    }
+    atomicAdd(&d.tag[base + w], (unsigned long long)(-(int64_t)PIN1));
+    return ost == ST_BUSY && tag_page(old) == page ? P_BUSY : P_MISS;
+  }
+  return P_MISS;
+}
+
+__device__ __forceinline__ void cache_unpin(const Dev &d, uint32_t line) {
+  atomicAdd(&d.tag[line], (unsigned long long)(-(int64_t)PIN1));
+}
+
+// Put back a victim we claimed but could not use (keeps transient pin bits of others).
+__device__ __forceinline__ void cache_unclaim(const Dev &d, uint32_t line, uint64_t old_tag) {
+  uint64_t cur = ld_rlx64(&d.tag[line]);
+  for (int i = 0; i < 64; ++i) {
+    uint64_t want = (old_tag & ~PIN_MASK) | (cur & PIN_MASK);
+    uint64_t got = atomicCAS(&d.tag[line], (unsigned long long)cur, (unsigned long long)want);
+    if (got == cur) return;
+    cur = got;
+  }
+}
+
+enum Miss { M_ISSUED = 0, M_HIT = 1, M_BUSY = 2, M_RETRY = 3 };
+
+struct Issued {
+  uint32_t q, slot, ticket;
+  int code;  // 1 fill, 2 evict READY, 3 write-back MODIFIED
+};
+
+// Cases (b) and (d) for one thread: take ownership of the page's miss in the share
+// table, pick a way (lowest INVALID way, else the clock: a set reference bit is
+// cleared and the hand moves on, the first unpinned, unreferenced READY or MODIFIED
+// way is the victim; BUSY, pinned and write-back-pending ways are skipped), reserve
+// queue slots, write back a MODIFIED victim from a staging copy and issue the read.
+// Nothing here waits: on any shortage every claim is undone and M_RETRY returned.
+//
+// fill=false (writes of whole pages): the caller already owns the page's share entry
+// `sh_own`; the way is claimed BUSY and returned without a read, the caller writes the
+// line and publishes it.  A MODIFIED victim is still written back first.
+static __device__ __noinline__ int cache_miss(const Dev &d, uint64_t page, uint32_t q0, uint32_t &line, Issued &is,
+                          bool fill = true, int64_t sh_own = -1) {
+  int64_t sh = sh_own;
+  if (fill) {
+    sh = sh_insert(d, page, SH_FILL);
+    if (sh < 0) {
+      atomicAdd(&d.stats[S_SHARE_RETRIES], 1ull);
+      return M_RETRY;
+    }
+  }
+  int pr = cache_probe(d, page, false, line);
+  if (pr != P_MISS) {
+    if (fill) sh_remove(d, (uint64_t)sh);
+    return pr == P_HIT ? M_HIT : M_BUSY;
+  }
+  uint32_t set = set_of(page, d.sets);
+  uint64_t base = (uint64_t)set * d.ways;
+  uint64_t claimed = tag_make(page, ST_BUSY, true);
+  int64_t victim = -1;
+  uint64_t old = 0;
+  int64_t sh_wb = -1;
+  for (uint32_t w = 0; w < d.ways && victim < 0; ++w) {
+    uint64_t t = ld_rlx64(&d.tag[base + w]);
+    if (t == 0 && atomicCAS(&d.tag[base + w], 0ull, (unsigned long long)claimed) == 0ull) victim = w;
+  }
+  for (uint32_t step = 0; victim < 0 && step < 2 * d.ways + 1; ++step) {
+    uint32_t w = atomicAdd(&d.hand[set], 1u) % d.ways;
+    uint64_t t = ld_rlx64(&d.tag[base + w]);
+    uint64_t st = tag_state(t);
+    if (st == ST_INVALID) {
+      if ((t & PIN_MASK) == 0 && atomicCAS(&d.tag[base + w], (unsigned long long)t, (unsigned long long)claimed) == t) {
+        victim = w;
+        old = 0;
+      }
+      continue;
+    }
+    if (st == ST_BUSY || (t & (PIN_MASK | TAG_WB))) continue;
+    if (t & TAG_REF) {
+      atomicAnd(&d.tag[base + w], ~TAG_REF);
+      continue;
+    }
+    if (st == ST_MODIFIED) {
+      sh_wb = sh_insert(d, tag_page(t), SH_WRITE);
+      if (sh_wb < 0) continue;
+    }
+    if (atomicCAS(&d.tag[base + w], (unsigned long long)t, (unsigned long long)claimed) == t) {
+      victim = w;
+      old = t;
+    } else if (sh_wb >= 0) {
+      sh_remove(d, (uint64_t)sh_wb);
+      sh_wb = -1;
+    }
+  }
+  if (victim < 0) {
+    if (fill) sh_remove(d, (uint64_t)sh);
+    atomicAdd(&d.stats[S_EAGAIN], 1ull);
+    return M_RETRY;
+  }
+  line = (uint32_t)(base + victim);
+  bool wb = tag_state(old) == ST_MODIFIED;
+  uint32_t q = 0, slot = 0, ticket = 0;
+  uint32_t nslots = (wb ? 1u : 0u) + (fill ? 1u : 0u);
+  if (nslots && !sq_reserve_any(d, q0, nslots, q, slot, ticket)) {
+    cache_unclaim(d, line, old);
+    if (wb) sh_remove(d, (uint64_t)sh_wb);
+    if (fill) sh_remove(d, (uint64_t)sh);
+    return M_RETRY;
+  }
+  is.q = q;
+  is.slot = slot;
+  is.ticket = ticket;
+  is.code = wb ? 3 : (old ? 2 : 1);
+  if (old) atomicAdd(&d.stats[S_EVICTIONS], 1ull);
+  if (wb) {
+    uint8_t *stg = d.staging + ((uint64_t)q * d.depth + slot) * kPage;
+    lane_copy_page(stg, line_ptr(d, line));
+    fence_ar();
+    sq_commit(d, q, slot, ticket, OP_WRITE, (uint64_t)stg, tag_page(old),
+              ctx_make(CTX_WB, (uint32_t)sh_wb, 0));
+    atomicAdd(&d.stats[S_WRITEBACKS], 1ull);
+    if (!fill) return M_ISSUED;  // the write-back is the command to ring
+    slot = (slot + 1) & d.dmask;
+    ticket += 1;
+  }
+  if (!fill) {
+    is.q = 0xFFFFFFFFu;  // nothing to ring
+    return M_ISSUED;
+  }
+  sq_commit(d, q, slot, ticket, OP_READ, (uint64_t)line_ptr(d, line), page,
+            ctx_make(CTX_FILL, (uint32_t)sh, line));
+  atomicAdd(&d.stats[S_MISSES], 1ull);
+  is.slot = slot;
+  is.ticket = ticket;
+  return M_ISSUED;
+}
+
+__device__ __forceinline__ uint64_t make_token(uint32_t q, uint32_t slot, uint32_t ticket) {
+  return ((uint64_t)q << 48) | ((uint64_t)slot << 32) | ticket;
+}
+
+// ---------------------------------------------------------------- warp-level requests
+// Sec. 3.3.2 two-level coalescing: lanes asking for the same page are matched with
+// __match_any_sync and only the lowest lane of each group goes to the cache.
+//
+// warp_request: every lane with `want` names a page.  Leaders probe; misses are issued
+// (one doorbell per queue per warp).  With wait=false this is a prefetch: the call
+// returns once every page is READY, in flight or could not be started.  With
+// wait=true it returns once every page is READY (no pins are held while waiting).
+// Returns false on timeout/abort.  `tok` (leaders) receives the token of the read the
+// lane itself issued, AGILE_TOKEN_HIT otherwise.
+static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint32_t q0, bool wait,
+                             uint64_t deadline, uint64_t *tok = nullptr, int *code = nullptr) {
+  unsigned grp = __match_any_sync(kFull, want ? page : ~0ull);
+  int lead_lane = __ffs(grp) - 1;
+  bool leader = want && lead_lane == (int)lane_id();
+  stat_warp(d, S_WARP_COALESCED, (want && !leader) ? 1u : 0u);
+  bool need = leader;
+  uint32_t line = 0;
+  bool ok = true;
+  bool first = true;
+  uint32_t ns = 64;
+  uint32_t retries = 0;
+  if (tok && leader) *tok = ~0ull;
+  if (code && leader) *code = 0;
+  while (__any_sync(kFull, need)) {
+    bool issued = false;
+    Issued is{};
+    if (need) {
+      int pr = cache_probe(d, page, false, line);
+      if (pr == P_HIT) {
+        need = false;
+        if (first) atomicAdd(&d.stats[S_HITS], 1ull);
+      } else if (pr == P_BUSY) {
+        if (first) atomicAdd(&d.stats[S_BUSY_HITS], 1ull);
+        if (!wait) need = false;
+      } else {
+        int m = cache_miss(d, page, q0, line, is);
+        if (m == M_ISSUED) {
+          issued = true;
+          if (tok) *tok = make_token(is.q, is.slot, is.ticket);
+          if (code) *code = is.code;
+          if (!wait) need = false;
+        } else if (m == M_HIT) {
+          need = false;
+        } else if (m == M_BUSY) {
+          if (!wait) need = false;
+        } else if (!wait && ++retries >= 4) {
+          need = false;  // a prefetch is a hint: give up when nothing can be evicted now
+        }
+      }
+    }
+    first = false;
+    if (!warp_ring(d, issued, is.q, is.slot, is.ticket, deadline)) ok = false;
+    if (__any_sync(kFull, need)) {
+      if (need) {
+        if (gtimer() > deadline || aborted(d)) {
+          set_error(d, -110);
+          need = false;
+          ok = false;
+        } else {
+          // wait for the in-flight line without holding anything, then re-probe
+          uint64_t t = ld_acq64(&d.tag[line]);
+          if (tag_page(t) == page && tag_state(t) == ST_BUSY) backoff(ns);
+          else if (!issued) backoff(ns);
+        }
+      }
+    }
+  }
+  return __all_sync(kFull, ok);
+}
+
+// The whole warp wants one page pinned (uniform `page`).  Lane 0 probes with a pin;
+// on a miss the warp issues and waits with nothing pinned, then probes again.
+// Returns the line in every lane, or false on timeout/abort.
+static __device__ bool warp_pin_page(const Dev &d, uint64_t page, uint32_t q0, uint64_t deadline,
+                              uint32_t &line_out) {
+  for (int round = 0;; ++round) {
+    uint32_t line = 0;
+    int pr = P_MISS;
+    if (lane_id() == 0) pr = cache_probe(d, page, true, line);
+    pr = __shfl_sync(kFull, pr, 0);
+    if (pr == P_HIT) {
+      line_out = __shfl_sync(kFull, line, 0);
+      if (lane_id() == 0 && round == 0) atomicAdd(&d.stats[S_HITS], 1ull);
+      return true;
+    }
+    if (!warp_request(d, lane_id() == 0, page, q0, true, deadline)) return false;
+    if (aborted(d)) return false;
+    if (gtimer() > deadline) {
+      if (lane_id() == 0) set_error(d, -110);
+      return false;
+    }
+  }
+}
+
+// ================================================================ completion side
+// Release what a completed command held (Sec. 3.2.1): the line becomes READY (or
+// INVALID on an error), the share-table entry is removed, the transaction barrier
+// (completion word) is set, the slot returns to EMPTY and the in-flight count drops.
+__device__ __forceinline__ void complete_command(const Dev &d, uint32_t q, uint32_t cid, uint32_t status) {
+  uint64_t i = (uint64_t)q * d.depth + cid;
+  uint64_t ctx = ld_rlx64(&d.cmd_ctx[i]);
+  uint64_t st = ld_rlx64(&d.sqe_state[i]);
+  uint64_t ticket = st >> 2;
+  uint64_t kind = ctx >> 60;
+  uint32_t sh = (uint32_t)(ctx >> 32) & 0x0FFFFFFFu;
+  uint32_t idx = (uint32_t)ctx;
+  fence_ar();
+  if (kind == CTX_FILL) {
+    if (status == 0) {
+      atomicAdd(&d.tag[idx], 1ull);  // BUSY (1) -> READY (2)
+    } else {
+      atomicAnd(&d.tag[idx], PIN_MASK);  // back to INVALID
+    }
+    sh_remove(d, sh);
+  } else if (kind == CTX_WB) {
+    if (idx) atomicAnd(&d.tag[idx - 1], ~TAG_WB);  // flush write-back from the line itself
+    sh_remove(d, sh);
+  }
+  if (status) atomicAdd(&d.stats[S_IO_ERRORS], 1ull);
+  st_rel64(&d.cmpl[i], ((ticket & 0xFFFFFFFFull) << 32) | ((uint64_t)(status & 0x7FFF) << 1) | 1ull);
+  st_rel64(&d.sqe_state[i], (ticket << 2) | SQE_EMPTY);
+  atomicAdd(&d.sq_resv[q], (unsigned long long)(-(int64_t)(1ull << 32)));
+}
+
+// Alg. 1, warp-centric CQ polling of queue q: lane l checks entry offset+l of the
+// current 32-entry window against the expected phase; the mask accumulates found
+// entries; a full mask advances the head and rings the CQ doorbell.
+static __device__ __noinline__ bool cq_poll(const Dev &d, uint32_t q) {
+  unsigned l = lane_id();
+  uint32_t *ps = &d.cq_poll[q * 4];
+  uint32_t offset = ld_rlx32(&ps[0]), mask = ld_rlx32(&ps[1]), phase = ld_rlx32(&ps[2]);
+  uint32_t found = 0, windows = 0;
+  for (int win = 0; win < 4; ++win) {
+    bool valid = false;
+    if (!((mask >> l) & 1u)) {
+      Cqe *c = &d.cq[(uint64_t)q * d.depth + offset + l];
+      uint32_t w3 = ld_acq32(&c->dw[3]);
+      if (((w3 >> 16) & 1u) == phase) {
+        complete_command(d, q, w3 & 0xFFFFu, w3 >> 17);
+        valid = true;
+      }
+    }
+    unsigned b = __ballot_sync(kFull, valid);
+    found += __popc(b);
+    mask |= b;
+    if (mask != kFull) break;
+    mask = 0;
+    offset += 32;
+    if (offset >= d.depth) {
+      offset = 0;
+      phase ^= 1u;
+    }
+    ++windows;
+    __syncwarp();
+    if (l == 0) {
+      fence_ar();
+      st_rel32(&d.cq_db[q], offset);
+    }
+  }
+  __syncwarp();
+  if (l == 0) {
+    st_rlx32(&ps[0], offset);
+    st_rlx32(&ps[1], mask);
+    st_rlx32(&ps[2], phase);
+    if (found) atomicAdd(&d.stats[S_CQES], (unsigned long long)found);
+    if (windows) atomicAdd(&d.stats[S_CQ_DOORBELLS], (unsigned long long)windows);
+  }
+  __syncwarp();
+  return found != 0;
+}
+
+// ================================================================ emulated device
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// One step of the device behind queue q (warp-collective): read the SQ doorbell,
+// stamp newly visible commands with their arrival time, then in order execute every
+// command whose latency and the queue's throughput budget allow: copy the page
+// between the store (pinned host memory over the host link) and HBM, and post a CQE
+// {SQ head, SQ id, CID, status, phase}.
+static __device__ __noinline__ bool emu_step(const Dev &d, uint32_t q, uint32_t max_cmds) {
+  unsigned l = lane_id();
+  uint32_t *es = &d.emu[q * 4];
+  uint32_t head = 0, ctail = 0, phase = 0, db = 0;
+  uint64_t now = gtimer();
+  if (l == 0) {
+    head = ld_rlx32(&es[0]);
+    ctail = ld_rlx32(&es[1]);
+    phase = ld_rlx32(&es[2]);
+    uint32_t seen = ld_rlx32(&es[3]);
+    db = ld_acq32(&d.sq_db[q]);
+    while (seen != db) {
+      st_rlx64(&d.emu_arrival[(uint64_t)q * d.depth + seen], now);
+      seen = (seen + 1) & d.dmask;
+    }
+    st_rlx32(&es[3], seen);
+  }
+  head = __shfl_sync(kFull, head, 0);
+  ctail = __shfl_sync(kFull, ctail, 0);
+  phase = __shfl_sync(kFull, phase, 0);
+  db = __shfl_sync(kFull, db, 0);
+  uint32_t done = 0;
+  uint64_t busy = 0;
+  if (l == 0) busy = ld_rlx64(&d.emu_busy[q]);
+  while (head != db && done < max_cmds) {
+    uint64_t i = (uint64_t)q * d.depth + head;
+    int go = 0;
+    uint32_t dw0 = 0, nlb = 0;
+    uint64_t prp1 = 0, slba = 0;
+    if (l == 0) {
+      uint64_t arr = ld_rlx64(&d.emu_arrival[i]);
+      uint64_t start = arr + d.lat_ns;
+      if (busy > start) start = busy;
+      go = now >= start;
+      if (go && ((ctail + 1) & d.dmask) == ld_acq32(&d.cq_db[q])) go = 0;  // CQ full
+      if (go) {
+        const uint32_t *e = d.sq[i].dw;
+        int4 a = ld_cg16(e), b = ld_cg16(e + 4), c = ld_cg16(e + 8), f = ld_cg16(e + 12);
+        dw0 = (uint32_t)a.x;
+        prp1 = (uint64_t)(uint32_t)b.z | ((uint64_t)(uint32_t)b.w << 32);
+        slba = (uint64_t)(uint32_t)c.z | ((uint64_t)(uint32_t)c.w << 32);
+        nlb = (uint32_t)f.x & 0xFFFFu;
+        busy = start + d.ns_per_page * (((uint64_t)nlb + 1) * 512 / kPage);
+      }
+    }
+    go = __shfl_sync(kFull, go, 0);
+    if (!go) break;
+    dw0 = __shfl_sync(kFull, dw0, 0);
+    prp1 = __shfl_sync(kFull, prp1, 0);
+    slba = __shfl_sync(kFull, slba, 0);
+    nlb = __shfl_sync(kFull, nlb, 0);
+    uint32_t opcode = dw0 & 0xFFu, cid = dw0 >> 16;
+    uint64_t nbytes = ((uint64_t)nlb + 1) * 512;
+    uint64_t off = slba * 512;
+    uint32_t status = 0;
+    bool drop = false;
+    if (d.fault_flags) {
+      uint64_t h = mix64(d.seed ^ ((uint64_t)q << 40) ^ ((uint64_t)ld_rlx64(&d.sqe_state[i]) >> 2));
+      if ((uint32_t)(h >> 32) < d.fault_thresh) {
+        if (d.fault_flags & 1u) status = 0x6;        // internal error
+        if (d.fault_flags & 2u) drop = true;
+      }
+    }
+    if (opcode != OP_FLUSH && (off + nbytes > d.store_bytes || nbytes != kPage)) status = 0x80;  // LBA out of range
+    if (status == 0 && opcode == OP_READ) {
+      warp_copy_page((void *)prp1, d.store + off);
+      if (l == 0) atomicAdd(&d.stats[S_BYTES_READ], (unsigned long long)nbytes);
+    } else if (status == 0 && opcode == OP_WRITE) {
+      warp_copy_page(d.store + off, (const void *)prp1);
+      if (l == 0) atomicAdd(&d.stats[S_BYTES_WRITTEN], (unsigned long long)nbytes);
+    }
+    __threadfence_system();
+    __syncwarp();
+    head = (head + 1) & d.dmask;
+    if (l == 0) {
+      atomicAdd(&d.stats[S_COMMANDS], 1ull);
+      if (!drop) {
+        Cqe *c = &d.cq[(uint64_t)q * d.depth + ctail];
+        st_rlx32(&c->dw[0], 0u);
+        st_rlx32(&c->dw[1], 0u);
+        st_rlx32(&c->dw[2], (q << 16) | head);
+        fence_ar();
+        st_rel32(&c->dw[3], cid | (phase << 16) | (status << 17));
+        ctail = (ctail + 1) & d.dmask;
+        if (ctail == 0) phase ^= 1u;
+      }
+    }
+    ctail = __shfl_sync(kFull, ctail, 0);
+    phase = __shfl_sync(kFull, phase, 0);
+    ++done;
+  }
+  if (l == 0) {
+    st_rlx32(&es[0], head);
+    st_rlx32(&es[1], ctail);
+    st_rlx32(&es[2], phase);
+    st_rlx64(&d.emu_busy[q], busy);
+  }
+  return done != 0;
+}
+
+// ================================================================ engine
+// One cooperative launch per library call.  Warp 0 of every CTA is a service warp:
+// it is the emulated device and the CQ poller for queues q = cta, cta + grid, ...
+// The other warps run the application.  No kernel of the library ever waits on
+// another launch: the device, the pollers and the waiters are co-resident warps of
+// one grid, and every wait is bounded by a deadline.
+static __device__ __noinline__ void service_loop(const Dev &d, uint32_t n_app, uint64_t deadline) {
+  uint32_t sw = blockIdx.x, nsw = gridDim.x;
+  uint32_t ns = 32;
+  for (;;) {
+    bool progress = false;
+    for (uint32_t q = sw; q < d.Q; q += nsw) {
+      progress |= emu_step(d, q, 8);
+      progress |= cq_poll(d, q);
+    }
+    if (progress) {
+      ns = 32;
+      continue;
+    }
+    uint32_t done = 0;
+    if (lane_id() == 0) done = ld_acq32(&d.run->app_done);
+    done = __shfl_sync(kFull, done, 0);
+    if (done >= n_app) {
+      bool drained = true;
+      for (uint32_t q = sw; q < d.Q; q += nsw)
+        if ((ld_acq64(&d.sq_resv[q]) >> 32) != 0) drained = false;
+      if (__all_sync(kFull, drained)) break;
+    }
+    if (gtimer() > deadline) {
+      if (lane_id() == 0) set_error(d, -110);
+      break;
+    }
+    __nanosleep(ns);
+    ns = ns < 256 ? ns * 2 : 256;
+  }
+}
+
+// Grid barrier over the application warps only (service warps never join).
+static __device__ bool app_barrier(const Dev &d, uint32_t n_app, uint64_t deadline) {
+  bool ok = true;
+  __syncwarp();
+  if (lane_id() == 0) {
+    fence_ar();
+    uint32_t gen = ld_acq32(&d.run->bar_gen);
+    uint32_t arrived = atomicAdd(&d.run->bar_count, 1u) + 1;
+    if (arrived == n_app) {
+      st_rlx32(&d.run->bar_count, 0u);
+      fence_ar();
+      st_rel32(&d.run->bar_gen, gen + 1);
+    } else {
+      uint32_t ns = 32;
+      while (ld_acq32(&d.run->bar_gen) == gen) {
+        if (gtimer() > deadline) {
+          set_error(d, -110);
+          ok = false;
+          break;
+        }
+        __nanosleep(ns);
+        ns = ns < 1024 ? ns * 2 : 1024;
+      }
+    }
+  }
+  ok = __shfl_sync(kFull, ok, 0);
+  __syncwarp();
+  return ok;
+}
+
+struct AppCtx {
+  uint32_t warp;     // app warp index in [0, n_warps)
+  uint32_t n_warps;  // app warps in the grid
+  uint32_t q0;       // this lane's home queue (Sec. 3.3.1: by thread index)
+  uint64_t deadline;
+};
+
+template <class App>
+__global__ void __launch_bounds__(kThreads) engine_kernel(Dev d, App app) {
+  uint32_t warp = threadIdx.x >> 5;
+  uint32_t n_app = gridDim.x * (kWarps - 1);
+  uint64_t deadline = gtimer() + d.timeout_ns;
+  if (warp == 0) {
+    service_loop(d, n_app, deadline + d.timeout_ns);
+    return;
+  }
+  AppCtx a;
+  a.warp = blockIdx.x * (kWarps - 1) + (warp - 1);
+  a.n_warps = n_app;
+  a.q0 = (uint32_t)(((uint64_t)a.warp * 32 + lane_id()) % d.Q);
+  a.deadline = deadline;
+  app.run(d, a);
+  __syncwarp();
+  if (lane_id() == 0) {
+    fence_ar();
+    atomicAdd(&d.run->app_done, 1u);
+  }
+}
+
+}  // namespace agile

@@ -1,0 +1,76 @@
+"""Helpers shared by the GPU tests: a context whose store holds given byte blobs."""
+from __future__ import annotations
+
+import numpy as np
+
+import paper_2504_19365_gb300 as ag
+
+PAGE = 4096
+
+
+def round_page(n: int) -> int:
+    return (int(n) + PAGE - 1) // PAGE * PAGE
+
+
+class Ctx:
+    def __init__(self, store_bytes: int, **cfg):
+        import torch
+        self.torch = torch
+        self.cfg = ag.agile_config_default(store_bytes=round_page(store_bytes), **cfg)
+        self.h = ag.agile_init(self.cfg)
+        self.stream = torch.cuda.current_stream().cuda_stream
+
+    def put(self, off: int, arr: np.ndarray):
+        a = np.ascontiguousarray(arr)
+        ag.agile_store_write(self.h, off, a.ctypes.data, a.nbytes)
+
+    def get(self, off: int, n: int) -> np.ndarray:
+        out = np.empty(n, dtype=np.uint8)
+        ag.agile_store_read(self.h, off, out.ctypes.data, n)
+        return out
+
+    def check(self):
+        e = ag.agile_check(self.h)
+        assert e == 0, f"device error {e}: {ag.strerror(e)}"
+
+    def stats(self):
+        return ag.agile_stats(self.h)
+
+    def tags(self) -> np.ndarray:
+        n = ag.agile_cache_lines(self.h)
+        out = np.zeros(n, dtype=np.uint64)
+        ag.agile_cache_tags(self.h, out.ctypes.data)
+        return out
+
+    def close(self):
+        if self.h:
+            ag.agile_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def tag_fields(tags: np.ndarray):
+    t = tags.astype(np.uint64)
+    return (t >> np.uint64(20)), (t & np.uint64(3)), ((t >> np.uint64(2)) & np.uint64(1)), \
+        ((t >> np.uint64(4)) & np.uint64(0xFFFF))
+
+
+def assert_cache_invariants(c: Ctx, store: np.ndarray | None = None):
+    """No two valid ways of a set hold one page; nothing pinned or in flight after a
+    call; every READY line equals the store page it caches."""
+    tags = c.tags()
+    page, state, _, pins = tag_fields(tags)
+    ways = c.cfg.ways
+    sets = len(tags) // ways
+    assert (pins == 0).all(), "pins left after the call"
+    assert not (state == 1).any(), "BUSY line after the call"
+    for s in range(sets):
+        sl = slice(s * ways, (s + 1) * ways)
+        valid = page[sl][state[sl] != 0]
+        assert len(valid) == len(set(valid.tolist())), f"duplicate tag in set {s}"
+    return page, state
