@@ -1,0 +1,428 @@
+#!/usr/bin/env python3
+"""Benchmark of the asynchronous GPU-centric I/O path (AGILE, arXiv 2504.19365).
+
+Headline workload (one step): breadth-first search over a seeded R-MAT graph
+(scale 20, edge factor 16, a=.57 b=.19 c=.19, symmetrised CSR with int64 offsets and
+int32 columns) that lives on the backing store (pinned host memory behind the
+emulated NVMe queues); the HBM cache holds 1/8 of the column array; one step runs the
+BFS from each of the 8 seeded sources, each from a cold cache with L2 flushed.
+Metric: CSR entries scanned per second (sum of the degrees of the reached vertices),
+asynchronous mode, sync mode reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload bfs|embedding]
+
+Under torchrun every rank runs an independent replica (the path has no exchange
+step); the value is the total work of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC_BFS = "BFS edges/s (async), RMAT scale 20 through a 1/8 HBM cache"
+METRIC_EMB = "embedding-bag lookups/s (async), 65,536x128 FP32 table through a 4 MiB cache"
+PAGE = 4096
+
+
+def round_page(n):
+    return (int(n) + PAGE - 1) // PAGE * PAGE
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    for d in ("paper_2504_19365_gb300/csrc", "include"):
+        for f in sorted(os.listdir(os.path.join(ROOT, d))):
+            with open(os.path.join(ROOT, d, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    cur = csrc_hash()
+    for line in open(path):
+        parts = dict(p.split("=", 1) for p in line.split() if "=" in p)
+        if parts.get("kernel") == kernel and parts.get("source") == cur:
+            try:
+                return float(parts["dram_bytes_per_launch"])
+            except (KeyError, ValueError):
+                return None
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.proc = None
+        self.gpu_id = gpu_id
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.result = self._collect()
+
+    def _collect(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ============================================================================ reference arm
+
+def run_reference(args):
+    """The CPU oracle, as it stands, on the host cores: the same workload, each step a
+    bounded sample of it."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    if args.workload == "bfs":
+        n, off, cols = synth.rmat_csr(3, 20, 16)
+        srcs = synth.bfs_sources(3, off, 8)
+
+        def step():
+            e = 0
+            for s in srcs:
+                e += oracle.bfs(off, cols, int(s))[1]
+            return e
+        unit, metric, sample = "edges/s", METRIC_BFS, "8 BFS from the seeded sources over the full graph"
+    else:
+        rows, dim = 65536, 128
+        T = synth.table_normal(1, rows, dim)
+        off = synth.bags_fixed(256, 16)
+        idx = [synth.indices_uniform(2, 4096, rows, offset=b * 4096) for b in range(16)]
+
+        def step():
+            for b in range(16):
+                oracle.embedding_bag(T, idx[b], off)
+            return 16 * 4096
+        unit, metric, sample = "lookups/s", METRIC_EMB, "16 batches x 256 bags x 16 indices"
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    work = 0
+    for _ in range(args.steps):
+        work += step()
+    dt = time.perf_counter() - t0
+    v = work / dt
+    line = {"impl": "reference", "metric": metric, "value": v, "unit": unit, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": args.workload},
+            "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_bfs(off, cols, srcs, budget_s=10.0):
+    import oracle
+    t0 = time.perf_counter()
+    e = 0
+    runs = 0
+    while True:
+        for s in srcs:
+            e += oracle.bfs(off, cols, int(s))[1]
+            runs += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": e / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": f"{runs} single-thread FIFO BFS runs over the full graph from the 8 seeded sources ({dt:.1f} s)"}
+
+
+# ============================================================================ our arm
+
+def measure_link_peak(torch, dev):
+    """Host-link read peak: pinned host -> HBM copy of 1 GiB, best of 3 (copy engine)."""
+    n = 1 << 30
+    h = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    d = torch.empty(n, dtype=torch.uint8, device=dev)
+    best = 0.0
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        d.copy_(h, non_blocking=True)
+        b.record()
+        b.synchronize()
+        best = max(best, n / (a.elapsed_time(b) * 1e-3) / 1e9)
+    del h, d
+    return best
+
+
+def run_bfs(args, torch, ag, dev, rank, world):
+    t_setup = time.perf_counter()
+    n, off, cols = synth.rmat_csr(3, 20, 16)
+    srcs = synth.bfs_sources(3, off, 8)
+    col0 = round_page(off.nbytes)
+    total = col0 + round_page(cols.nbytes)
+    ways = 8
+    lines = max(ways, (cols.nbytes // 8 + PAGE - 1) // PAGE)
+    cache_bytes = (lines + ways - 1) // ways * ways * PAGE
+    cfg = ag.agile_config_default(store_bytes=total, cache_bytes=cache_bytes, ways=ways,
+                                  device=torch.cuda.current_device())
+    ctx = ag.agile_init(cfg)
+    stream = torch.cuda.current_stream().cuda_stream
+    ag.agile_store_write(ctx, 0, off.ctypes.data, off.nbytes)
+    ag.agile_store_write(ctx, col0, cols.ctypes.data, cols.nbytes)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    level = torch.empty(n, dtype=torch.int32, device=dev)
+    edges = torch.zeros(1, dtype=torch.int64, device=dev)
+    h_level = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    h_edges = torch.empty(1, dtype=torch.int64, pin_memory=True)
+    ctas, _ = ag.agile_launch_shape(ctx)
+
+    def one(src, mode, e2e=False):
+        ag.agile_invalidate(ctx, stream)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ag.agile_bfs(ctx, 0, col0, n, int(src), level.data_ptr(), edges.data_ptr(), mode, stream)
+        if e2e:
+            h_level.copy_(level, non_blocking=True)
+            h_edges.copy_(edges, non_blocking=True)
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b), int(edges.item())
+
+    def steps(mode, k, e2e=False):
+        ms, work = 0.0, 0
+        for _ in range(k):
+            for s in srcs:
+                t, e = one(s, mode, e2e)
+                ms += t
+                work += e
+        return ms, work
+
+    setup_s = time.perf_counter() - t_setup
+    steps(ag.AGILE_ASYNC, args.warmup)
+    steps(ag.AGILE_SYNC, max(1, args.warmup // 2))
+    err = ag.agile_check(ctx)
+    if err:
+        raise RuntimeError(f"device error during warm-up: {ag.strerror(err)}")
+    # reached vertices and moved bytes per BFS (outside the timed region)
+    ag.agile_reset_stats(ctx)
+    reached = []
+    for s in srcs:
+        one(s, ag.AGILE_ASYNC)
+        reached.append(int((level >= 0).sum().item()))
+    st = ag.agile_stats(ctx)
+    moved_per_bfs = st["bytes_read"] / len(srcs)
+    misses_per_bfs = st["misses"] / len(srcs)
+    hit_rate = st["hits"] / max(1, st["hits"] + st["misses"])
+
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid).replace("GPU-", "")
+    except Exception:
+        gpu_id = None
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(gpu_id) as clk:
+        ms_async, work_async = steps(ag.AGILE_ASYNC, args.steps)
+        torch.cuda.synchronize()
+    clocks = clk.result
+    ms_sync, work_sync = steps(ag.AGILE_SYNC, args.steps)
+    ms_e2e, work_e2e = steps(ag.AGILE_ASYNC, args.steps, e2e=True)
+    err = ag.agile_check(ctx)
+    if err:
+        raise RuntimeError(f"device error: {ag.strerror(err)}")
+
+    vals = torch.tensor([ms_async, ms_sync, ms_e2e], dtype=torch.float64, device=dev)
+    wk = torch.tensor([work_async, work_sync, work_e2e], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(wk, op=torch.distributed.ReduceOp.SUM)
+    ms_async, ms_sync, ms_e2e = vals.tolist()
+    work_async, work_sync, work_e2e = wk.tolist()
+    link_peak = measure_link_peak(torch, dev)
+    launches = args.steps * len(srcs)
+    t_launch = ms_async / launches * 1e-3
+    edges_per_bfs = work_async / world / launches
+    algo_bytes = 4.0 * edges_per_bfs + 16.0 * statistics.mean(reached)
+    achieved = algo_bytes / t_launch / 1e9
+    result = {
+        "metric": METRIC_BFS,
+        "value": work_async / (ms_async * 1e-3),
+        "unit": "edges/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_async / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "bfs_rmat20_ef16_cache1/8", "graph": {"vertices": n, "csr_entries": int(cols.size),
+                   "a": 0.57, "b": 0.19, "c": 0.19, "seed": 3}, "sources": [int(s) for s in srcs],
+                   "cache_bytes": cache_bytes, "ways": ways, "queues": cfg.num_queues, "depth": cfg.queue_depth,
+                   "emulated_device": "pinned host memory, no latency model", "ctas": ctas,
+                   "l2": "flushed (256 MiB write) and HBM cache invalidated before every BFS, untimed",
+                   "parallelism": f"replicas x{world}"},
+        "sync": {"value": work_sync / (ms_sync * 1e-3), "unit": "edges/s", "ms_per_step": ms_sync / args.steps},
+        "async_over_sync": ms_sync / ms_async,
+        "roofline": {"bound": "host_link", "achieved": achieved, "peak": link_peak, "unit": "GB/s",
+                     "frac": achieved / link_peak, "traffic": recorded_traffic("engine_kernel<BfsApp>"),
+                     "kernel": "engine_kernel<BfsApp>",
+                     "algorithmic_bytes_per_launch": algo_bytes,
+                     "peak_source": "measured in this run: pinned host->HBM copy of 1 GiB (copy engine)",
+                     "moved_bytes_per_launch": moved_per_bfs,
+                     "moved_gbs": moved_per_bfs / t_launch / 1e9,
+                     "moved_frac": moved_per_bfs / t_launch / 1e9 / link_peak,
+                     "misses_per_launch": misses_per_bfs, "hit_rate": hit_rate},
+        "e2e": {"value": work_e2e / (ms_e2e * 1e-3), "unit": "edges/s",
+                "h2d_bytes_per_step": moved_per_bfs * len(srcs),
+                "d2h_bytes_per_step": (n * 4 + 8) * len(srcs)},
+        "gpu_launches": 2 * launches,
+        "clocks": clocks,
+        "setup_s": setup_s,
+    }
+    ag.agile_destroy(ctx)
+    return result, (off, cols, srcs)
+
+
+def run_embedding(args, torch, ag, dev, rank, world):
+    rows, dim, nb, pool, batches = 65536, 128, 256, 16, 16
+    T = synth.table_normal(1, rows, dim)
+    off = synth.bags_fixed(nb, pool)
+    idx = np.concatenate([synth.indices_uniform(2, nb * pool, rows, offset=b * nb * pool) for b in range(batches)])
+    cfg = ag.agile_config_default(store_bytes=T.nbytes, cache_bytes=4 << 20, ways=8,
+                                  device=torch.cuda.current_device())
+    ctx = ag.agile_init(cfg)
+    stream = torch.cuda.current_stream().cuda_stream
+    ag.agile_store_write(ctx, 0, T.ctypes.data, T.nbytes)
+    d_idx = torch.from_numpy(idx).to(dev)
+    d_off = torch.from_numpy(off).to(dev)
+    out = torch.empty((batches, nb, dim), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(mode):
+        ag.agile_invalidate(ctx, stream)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for bt in range(batches):
+            ag.agile_embedding_bag(ctx, 0, rows, dim, d_idx.data_ptr() + bt * nb * pool * 8, d_off.data_ptr(), nb,
+                                   out[bt].data_ptr(), mode, stream)
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b)
+
+    for _ in range(args.warmup):
+        step(ag.AGILE_ASYNC)
+        step(ag.AGILE_SYNC)
+    ms_a = sum(step(ag.AGILE_ASYNC) for _ in range(args.steps))
+    ms_s = sum(step(ag.AGILE_SYNC) for _ in range(args.steps))
+    err = ag.agile_check(ctx)
+    if err:
+        raise RuntimeError(f"device error: {ag.strerror(err)}")
+    ag.agile_destroy(ctx)
+    look = batches * nb * pool * args.steps
+    return {"async": look / (ms_a * 1e-3), "sync": look / (ms_s * 1e-3), "unit": "lookups/s",
+            "ms_per_step_async": ms_a / args.steps, "ms_per_step_sync": ms_s / args.steps,
+            "workload": "65,536x128 FP32 table, 4 MiB 8-way cache, 16 batches x 256 bags x 16 uniform indices"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="bfs", choices=["bfs", "embedding"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+
+    import paper_2504_19365_gb300 as ag
+    from paper_2504_19365_gb300 import build as _b
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        _b.build()
+    if world > 1:
+        torch.distributed.barrier()
+    _b.build()  # no-op when up to date
+    if args.workload == "bfs":
+        res, graph = run_bfs(args, torch, ag, dev, rank, world)
+        if not args.no_extras:
+            res["embedding_bag"] = run_embedding(args, torch, ag, dev, rank, world)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline_bfs(*graph)
+    else:
+        e = run_embedding(args, torch, ag, dev, rank, world)
+        res = {"metric": METRIC_EMB, "value": e["async"], "unit": "lookups/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": e["ms_per_step_async"],
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic", "config": {"workload": e["workload"]}, "sync": e["sync"]}
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

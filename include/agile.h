@@ -97,6 +97,8 @@ typedef struct {
   uint64_t seed;            /* seed of the fault injector                             */
   uint32_t max_ctas;        /* cap on CTAs per launch (0 = all co-resident CTAs)      */
   uint32_t prefetch_depth;  /* async lookahead in work units (0 = default 1)          */
+  uint32_t app_warps;       /* cap on application warps per call (0 = sized from the
+                               cache so the warps' working set fits in it)           */
 } agile_config;
 
 typedef struct {

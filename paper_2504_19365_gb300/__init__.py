@@ -57,6 +57,7 @@ class agile_config(C.Structure):
         ("seed", C.c_uint64),
         ("max_ctas", C.c_uint32),
         ("prefetch_depth", C.c_uint32),
+        ("app_warps", C.c_uint32),
     ]
 
 

@@ -122,83 +122,142 @@ struct EmbApp {
 // vertex and takes part when level[v] == L.  Its offsets[v], offsets[v+1] (int64) and
 // its neighbour list (int32) are read through the cache; every neighbour u with
 // level[u] == -1 gets level L+1 by compare-and-swap.  Vertices are visited in id order,
-// so neighbouring lists that share a page are read while the page is resident.  A grid
-// barrier over the app warps ends each level; the search stops when a level discovers
+// so neighbouring lists that share a page are read while the page is resident.
+// A list of at least kHub entries is not scanned by the warp that found it: it goes
+// to a queue of long lists, cut into slices of kSlice entries that any warp may take,
+// so one hub cannot hold up a level.  Every warp drains that queue before it reaches
+// the grid barrier that ends the level; the search stops when a level discovers
 // nothing.  Edges scanned = sum of the degrees of the frontier vertices of all levels.
 //   SYNC : each page (offsets, columns) is requested when needed and waited for.
-//   ASYNC: before scanning a chunk, all column pages of its frontier vertices are
-//          issued at once; offsets pages of the next chunk are issued ahead.
+//   ASYNC: the offsets pages of a sub-chunk and the first 32 pages of its column span
+//          are issued before any of them is read.
+// A warp keeps at most one line pinned between steps (the page it read last) and lets
+// it go before it requests or waits for any other page.
+struct HubEntry {
+  long long s, e;
+  unsigned int next;   // next slice to hand out
+  unsigned int ready;  // level + 1 once s and e are written
+};
+
 struct BfsApp {
   uint64_t off_page0, col_page0;
   uint32_t n;
   int32_t *level;
   unsigned long long *edges_out;
   uint32_t mode;
+  HubEntry *hubq;
+  uint32_t hub_cap;
 
   static constexpr uint32_t kChunk = 128;
+  static constexpr uint32_t kHub = 1024;
+  static constexpr uint32_t kSlice = 2048;
 
-  // read an int64 (offsets) or int32 (columns) element at byte `byte` of the array
-  // starting at store page `page0`, for lanes with `want`, through the cache: the warp
-  // walks the distinct pages of the requests, pinning each one for its reads only.
+  struct Pin {
+    uint64_t page;
+    uint32_t line;
+    bool valid;
+  };
+
+  __device__ __forceinline__ void release(const Dev &d, Pin &pc) const {
+    if (pc.valid) {
+      __syncwarp();
+      if (lane_id() == 0) cache_unpin(d, pc.line);
+      pc.valid = false;
+    }
+  }
+
+  // Element at byte `byte` of the array at store page `page0`, for lanes with `want`,
+  // through the cache: the warp walks the distinct pages of the requests.
   template <typename T>
-  __device__ bool gather(const Dev &d, const AppCtx &a, uint64_t page0, bool want, uint64_t byte, T &val) const {
+  __device__ bool gather(const Dev &d, const AppCtx &a, uint64_t page0, bool want, uint64_t byte, T &val,
+                         Pin &pc) const {
     uint64_t pg = page0 + byte / kPage;
     uint32_t in = (uint32_t)(byte % kPage);
     bool todo = want;
-    while (__any_sync(kFull, todo)) {
-      unsigned m = __ballot_sync(kFull, todo);
-      uint64_t p = __shfl_sync(kFull, pg, __ffs(m) - 1);
-      uint32_t line;
-      if (!warp_pin_page(d, p, a.q0, a.deadline, line)) return false;
-      if (todo && pg == p) {
-        const uint8_t *src = line_ptr(d, line) + in;
+    for (;;) {
+      if (pc.valid && todo && pg == pc.page) {
+        const uint8_t *src = line_ptr(d, pc.line) + in;
         if (sizeof(T) == 8) val = (T)ld_cg_s64(src);
         else val = (T)ld_cg_s32(src);
         todo = false;
       }
-      __syncwarp();
-      if (lane_id() == 0) cache_unpin(d, line);
+      unsigned m = __ballot_sync(kFull, todo);
+      if (!m) return true;
+      uint64_t p = __shfl_sync(kFull, pg, __ffs(m) - 1);
+      release(d, pc);
+      uint32_t line;
+      if (!warp_pin_page(d, p, a.q0, a.deadline, line)) return false;
+      pc.page = p;
+      pc.line = line;
+      pc.valid = true;
     }
-    return true;
+  }
+
+  __device__ __forceinline__ void visit(bool act, int32_t u, int32_t L, uint32_t &found) const {
+    if (act && (uint32_t)u < n) {
+      if (ld_rlx32((const uint32_t *)&level[u]) == 0xFFFFFFFFu && atomicCAS((int *)&level[u], -1, L + 1) == -1)
+        found++;
+    }
   }
 
   __device__ bool chunk(const Dev &d, const AppCtx &a, uint32_t v0, int32_t L, uint32_t &found,
-                        unsigned long long &scanned) const {
+                        unsigned long long &scanned, Pin &pc) const {
     unsigned l = lane_id();
     uint32_t v = v0 + l;
     bool f = v < n && ld_rlx32((const uint32_t *)&level[v]) == (uint32_t)L;
     if (!__any_sync(kFull, f)) return true;
     const bool async = mode == AGILE_ASYNC;
-    // offsets[v], offsets[v+1]
     if (async) {
-      if (!warp_request(d, f, off_page0 + ((uint64_t)v * 8) / kPage, a.q0, false, a.deadline)) return false;
-      if (!warp_request(d, f, off_page0 + ((uint64_t)v * 8 + 8) / kPage, a.q0, false, a.deadline)) return false;
+      uint64_t pa = off_page0 + ((uint64_t)v * 8) / kPage, pb = off_page0 + ((uint64_t)v * 8 + 8) / kPage;
+      bool need_a = f && !(pc.valid && pc.page == pa), need_b = f && pb != pa && !(pc.valid && pc.page == pb);
+      if (__any_sync(kFull, need_a) && !warp_request(d, need_a, pa, a.q0, false, a.deadline)) return false;
+      if (__any_sync(kFull, need_b) && !warp_request(d, need_b, pb, a.q0, false, a.deadline)) return false;
     }
     int64_t s = 0, e = 0;
-    if (!gather<int64_t>(d, a, off_page0, f, (uint64_t)v * 8, s)) return false;
-    if (!gather<int64_t>(d, a, off_page0, f, (uint64_t)v * 8 + 8, e)) return false;
+    if (!gather<int64_t>(d, a, off_page0, f, (uint64_t)v * 8, s, pc)) return false;
+    if (!gather<int64_t>(d, a, off_page0, f, (uint64_t)v * 8 + 8, e, pc)) return false;
     uint32_t deg = f ? (uint32_t)(e - s) : 0;
-    // exclusive prefix of the degrees over the warp
-    uint32_t incl = deg;
+    scanned += __reduce_add_sync(kFull, deg);
+    // long lists go to the slice queue
+    bool hub = deg >= kHub;
+    if (__any_sync(kFull, hub)) {
+      if (hub) {
+        uint32_t idx = atomicAdd(&d.run->hub_count[L & 1], 1u);
+        if (idx < hub_cap) {
+          HubEntry *h = &hubq[idx];
+          h->s = s;
+          h->e = e;
+          h->next = 0;
+          __threadfence();
+          st_rel32(&h->ready, (uint32_t)L + 1);
+        } else {
+          hub = false;  // queue full: scanned here
+        }
+      }
+    }
+    uint32_t dg = hub ? 0 : deg;
+    uint32_t incl = dg;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       uint32_t t = __shfl_up_sync(kFull, incl, o);
       if (l >= (unsigned)o) incl += t;
     }
-    uint32_t excl = incl - deg;
+    uint32_t excl = incl - dg;
     uint32_t total = __shfl_sync(kFull, incl, 31);
-    scanned += total;
     if (total == 0) return true;
     if (async) {
-      // issue every column page of the chunk's frontier lists, page by page per lane
-      uint64_t cp0 = col_page0 + ((uint64_t)s * 4) / kPage;
-      uint64_t cp1 = deg ? col_page0 + ((uint64_t)(e - 1) * 4) / kPage : cp0;
-      for (uint64_t k = 0;; ++k) {
-        bool want = deg && cp0 + k <= cp1;
-        if (!__any_sync(kFull, want)) break;
-        if (!warp_request(d, want, cp0 + k, a.q0, false, a.deadline)) return false;
-        if (k >= 64) break;  // very long lists are fetched on demand past this point
+      // the lists of 32 consecutive vertices lie in one contiguous span of the column
+      // array: issue its first 32 pages at once
+      int64_t lo = dg ? s : INT64_MAX, hi = dg ? e - 1 : -1;
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        lo = min(lo, (int64_t)__shfl_xor_sync(kFull, lo, o));
+        hi = max(hi, (int64_t)__shfl_xor_sync(kFull, hi, o));
       }
+      uint64_t p0 = col_page0 + ((uint64_t)lo * 4) / kPage, p1 = col_page0 + ((uint64_t)hi * 4) / kPage;
+      uint64_t pg = p0 + l;
+      bool want = pg <= p1 && !(pc.valid && pc.page == pg);
+      if (__any_sync(kFull, want) && !warp_request(d, want, pg, a.q0, false, a.deadline)) return false;
     }
     for (uint32_t k0 = 0; k0 < total; k0 += 32) {
       uint32_t k = k0 + l;
@@ -215,14 +274,53 @@ struct BfsApp {
       uint32_t exj = __shfl_sync(kFull, excl, j);
       uint64_t pos = (uint64_t)sj + (k - exj);
       int32_t u = 0;
-      if (!gather<int32_t>(d, a, col_page0, act, pos * 4, u)) return false;
-      if (act && (uint32_t)u < n) {
-        if (ld_rlx32((const uint32_t *)&level[u]) == 0xFFFFFFFFu &&
-            atomicCAS((int *)&level[u], -1, L + 1) == -1)
-          found++;
-      }
+      if (!gather<int32_t>(d, a, col_page0, act, pos * 4, u, pc)) return false;
+      visit(act, u, L, found);
     }
     return true;
+  }
+
+  // take slices of the queued long lists of level L until none is left
+  __device__ bool help_hubs(const Dev &d, const AppCtx &a, int32_t L, uint32_t &found, Pin &pc) const {
+    unsigned l = lane_id();
+    uint32_t ns = 64;
+    for (;;) {
+      uint32_t c = 0;
+      if (l == 0) c = ld_acq32(&d.run->hub_count[L & 1]);
+      c = min(__shfl_sync(kFull, c, 0), hub_cap);
+      bool pending = false;
+      for (uint32_t i = 0; i < c; ++i) {
+        HubEntry *h = &hubq[i];
+        uint32_t rd = 0;
+        if (l == 0) rd = ld_acq32(&h->ready);
+        rd = __shfl_sync(kFull, rd, 0);
+        if (rd != (uint32_t)L + 1) {
+          pending = true;
+          continue;
+        }
+        int64_t s = ld_cg_s64(&h->s), e = ld_cg_s64(&h->e);
+        uint32_t slices = (uint32_t)((e - s + kSlice - 1) / kSlice);
+        for (;;) {
+          uint32_t k = 0;
+          if (l == 0) k = atomicAdd(&h->next, 1u);
+          k = __shfl_sync(kFull, k, 0);
+          if (k >= slices) break;
+          int64_t p0 = s + (int64_t)k * kSlice, p1 = min(e, p0 + (int64_t)kSlice);
+          for (int64_t pos = p0 + l; pos - l < p1; pos += 32) {
+            bool act = pos < p1;
+            int32_t u = 0;
+            if (!gather<int32_t>(d, a, col_page0, act, (uint64_t)(act ? pos : p0) * 4, u, pc)) return false;
+            visit(act, u, L, found);
+          }
+        }
+      }
+      if (!pending) return true;
+      if (gtimer() > a.deadline || aborted(d)) {
+        if (l == 0) set_error(d, -110);
+        return false;
+      }
+      backoff(ns);
+    }
   }
 
   __device__ void run(const Dev &d, const AppCtx &a) const {
@@ -231,21 +329,26 @@ struct BfsApp {
     unsigned long long scanned = 0;
     for (int32_t L = 0;; ++L) {
       if (a.warp == 0 && l == 0) {
-        // the chunk counter of level L+1 was last used at level L-1, whose chunks were
-        // all claimed before barrier L-1; the discovery counter of level L+1 (three
-        // slots) was last read right after barrier L-2, which every warp has left
+        // the counters of level L+1 were last used at level L-1, whose work every warp
+        // finished before barrier L-1; the discovery counter of level L+1 (three slots)
+        // was last read right after barrier L-2, which every warp has left
         st_rlx32(&d.run->work[(L + 1) & 1], 0u);
+        st_rlx32(&d.run->hub_count[(L + 1) & 1], 0u);
         st_rlx64(&d.run->acc[1 + (L + 1) % 3], 0ull);
       }
       uint32_t found = 0;
+      Pin pc{0, 0, false};
+      bool ok = true;
       for (;;) {
         uint32_t c = 0;
         if (l == 0) c = atomicAdd(&d.run->work[L & 1], 1u);
         c = __shfl_sync(kFull, c, 0);
         if (c >= nchunks || aborted(d)) break;
-        for (uint32_t sub = 0; sub < kChunk; sub += 32)
-          if (!chunk(d, a, c * kChunk + sub, L, found, scanned)) break;
+        for (uint32_t sub = 0; sub < kChunk && ok; sub += 32) ok = chunk(d, a, c * kChunk + sub, L, found, scanned, pc);
+        if (!ok) break;
       }
+      if (ok) help_hubs(d, a, L, found, pc);
+      release(d, pc);
       uint32_t tot = __reduce_add_sync(kFull, found);
       if (l == 0 && tot) atomicAdd(&d.run->acc[1 + L % 3], (unsigned long long)tot);
       if (!app_barrier(d, a.n_warps, a.deadline)) return;
@@ -280,7 +383,7 @@ int agile_embedding_bag(agile_ctx *c, uint64_t table_byte0, uint32_t rows, uint3
   // rows must not straddle pages: dim*4 divides the page
   if (kPage % (dim * 4)) return AGILE_EINVAL;
   EmbApp app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, mode};
-  return launch_engine(c, app, stream);
+  return launch_engine(c, app, stream, warps_for_cache(c, mode == AGILE_ASYNC ? 48 : 4, 32));
 }
 
 int agile_bfs(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_t n_vertices, int32_t src,
@@ -295,9 +398,19 @@ int agile_bfs(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_
   bfs_init_kernel<<<(n_vertices + 255) / 256, 256, 0, s>>>(d_level, n_vertices, src);
   AGILE_CUDA_TRY(cudaGetLastError());
   if (d_edges_scanned) AGILE_CUDA_TRY(cudaMemsetAsync(d_edges_scanned, 0, 8, s));
+  // queue of long lists: at most (column entries) / kHub of them per level
+  uint64_t cap = (c->cfg.store_bytes - cols_byte0) / 4 / BfsApp::kHub + 1;
+  if (cap > (1u << 22)) cap = 1u << 22;
+  if (cap < 1024) cap = 1024;
+  if (!c->bfs_hubq || c->bfs_hub_cap < cap) {
+    if (c->bfs_hubq) cudaFree(c->bfs_hubq);
+    c->bfs_hubq = nullptr;
+    AGILE_CUDA_TRY(cudaMalloc(&c->bfs_hubq, cap * sizeof(HubEntry)));
+    c->bfs_hub_cap = (uint32_t)cap;
+  }
   BfsApp app{offsets_byte0 / kPage, cols_byte0 / kPage, n_vertices, d_level,
-             (unsigned long long *)d_edges_scanned, mode};
-  return launch_engine(c, app, stream);
+             (unsigned long long *)d_edges_scanned, mode, (HubEntry *)c->bfs_hubq, c->bfs_hub_cap};
+  return launch_engine(c, app, stream, warps_for_cache(c, 4, 32));
 }
 
 }  // extern "C"

@@ -8,6 +8,8 @@
 #include "agile.h"
 #include "agile_dev.cuh"
 
+#include <algorithm>
+
 struct agile_ctx {
   agile_config cfg;
   int device = 0;
@@ -16,6 +18,8 @@ struct agile_ctx {
   void *store_host = nullptr;
   std::vector<void *> dallocs;
   int last_cuda_error = 0;
+  void *bfs_hubq = nullptr;  // BFS scratch: queue of long adjacency lists
+  uint32_t bfs_hub_cap = 0;
 };
 
 namespace agile {
@@ -30,6 +34,13 @@ namespace agile {
   } while (0)
 
 inline cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
+
+// Application warps for a call whose warps each keep about `pages_per_warp` lines busy:
+// enough warps to keep the queues fed, few enough that their pages fit in the cache.
+inline uint32_t warps_for_cache(const agile_ctx *c, uint64_t pages_per_warp, uint32_t floor_warps) {
+  uint64_t w = c->dev.nlines / (pages_per_warp ? pages_per_warp : 1);
+  return (uint32_t)std::max<uint64_t>(floor_warps, w);
+}
 
 // Largest co-resident grid for this engine instantiation (cooperative launch rule:
 // every CTA must be resident at once, because the service warps and the waiting app
@@ -48,14 +59,17 @@ int engine_grid(agile_ctx *c) {
   return g;
 }
 
+// `active`: application warps the call wants (0 = every app warp of the grid); the
+// context's app_warps setting overrides it.
 template <class App>
-int launch_engine(agile_ctx *c, const App &app, void *stream, int grid_override = 0) {
+int launch_engine(agile_ctx *c, const App &app, void *stream, uint32_t active = 0) {
   cudaStream_t s = as_stream(stream);
   AGILE_CUDA_TRY(cudaSetDevice(c->device));
-  int grid = grid_override > 0 ? grid_override : engine_grid<App>(c);
+  int grid = engine_grid<App>(c);
   if (grid <= 0) return AGILE_ECUDA;
   AGILE_CUDA_TRY(cudaMemsetAsync(c->dev.run, 0, sizeof(RunState), s));
   Dev d = c->dev;
+  d.app_active = c->cfg.app_warps ? c->cfg.app_warps : active;
   App a = app;
   void *args[] = {(void *)&d, (void *)&a};
   AGILE_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)engine_kernel<App>, dim3(grid), dim3(kThreads),

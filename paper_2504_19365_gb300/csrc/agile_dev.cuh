@@ -6,7 +6,7 @@
 //   hand       [sets]   u32         clock hand per set (Sec. 4.4, clock policy)
 //   sh_key/val [buckets*4] u64      in-flight share table, 4 slots per bucket (Sec. 3.4.1)
 //   sq         [Q * depth] 64 B     NVMe submission entries (Sec. 2.1)
-//   cq         [Q * depth] 16 B     NVMe completion entries with phase bit (Sec. 2.1)
+//   cq         [Q * 2*depth] 16 B   NVMe completion entries with phase bit (Sec. 2.1)
 //   sqe_state  [Q * depth] u64      {ticket:62 | EMPTY/UPDATED/ISSUED} (Sec. 3.3.1)
 //   cmd_ctx    [Q * depth] u64      what a completion releases (line fill, write-back)
 //   cmpl       [Q * depth] u64      completion word = transaction barrier (Sec. 3.2.1)
@@ -14,7 +14,7 @@
 //   sq_tail/sq_lock/sq_db [Q] u32   doorbell-lock holder's tail, the lock, doorbell
 //   cq_db      [Q] u32              CQ head doorbell
 //   cq_poll    [Q*4] u32            Alg. 1 state {offset, mask, phase}
-//   emu*                            emulated device: fetch head, CQ tail, phase, timing
+//   emu*                            emulated device: fetch/seen/CQ-slot counters, timing
 //   staging    [Q * depth * 4096]   write-back sources, one page per submission slot
 #pragma once
 #include <cstdint>
@@ -70,6 +70,7 @@ struct RunState {
   uint32_t work[4];       // dynamic work counters
   unsigned long long acc[4];  // accumulators (edges scanned, discovered vertices, ...)
   uint32_t flag[4];
+  uint32_t hub_count[2];  // BFS: long adjacency lists queued for slicing, per level parity
 };
 
 struct Dev {
@@ -87,6 +88,7 @@ struct Dev {
   uint32_t sh_mask;  // buckets - 1 (power of two)
   // queues
   uint32_t Q, depth, dmask, dlog;
+  uint32_t cq_size;  // CQ entries per queue = 2 * depth
   Sqe *sq;
   Cqe *cq;
   unsigned long long *sqe_state;
@@ -94,7 +96,7 @@ struct Dev {
   unsigned long long *cmpl;
   unsigned long long *sq_resv;
   uint32_t *sq_tail, *sq_lock, *sq_db, *cq_db, *cq_poll;
-  uint32_t *emu;  // [Q*4] {sq_head, cq_tail, cq_phase, seen}
+  uint32_t *emu;  // [Q*4] device counters {fetch, seen, cq slot, -}
   unsigned long long *emu_busy;     // [Q] ns at which the queue's device pipe is free
   unsigned long long *emu_arrival;  // [Q*depth] ns at which the device saw the command
   uint8_t *staging;
@@ -108,6 +110,7 @@ struct Dev {
   uint64_t timeout_ns;
   uint32_t prefetch_depth;
   int32_t *err_sticky;  // first error since the last agile_check
+  uint32_t app_active;  // application warps that take part in this launch (0 = all)
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -468,7 +471,7 @@ struct Issued {
 // fill=false (writes of whole pages): the caller already owns the page's share entry
 // `sh_own`; the way is claimed BUSY and returned without a read, the caller writes the
 // line and publishes it.  A MODIFIED victim is still written back first.
-static __device__ __noinline__ int cache_miss(const Dev &d, uint64_t page, uint32_t q0, uint32_t &line, Issued &is,
+static __device__ int cache_miss(const Dev &d, uint64_t page, uint32_t q0, uint32_t &line, Issued &is,
                           bool fill = true, int64_t sh_own = -1) {
   int64_t sh = sh_own;
   if (fill) {
@@ -639,18 +642,48 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
   return __all_sync(kFull, ok);
 }
 
-// The whole warp wants one page pinned (uniform `page`).  Lane 0 probes with a pin;
-// on a miss the warp issues and waits with nothing pinned, then probes again.
-// Returns the line in every lane, or false on timeout/abort.
+// Warp-cooperative probe of one page (uniform across the warp): lane w < ways loads
+// the tag of way w, so the whole set is read in one round trip; on a READY/MODIFIED
+// match the matching lane pins the line.  Same outcome as cache_probe(pin=true).
+__device__ __forceinline__ int warp_probe_pin(const Dev &d, uint64_t page, uint32_t &line) {
+  unsigned l = lane_id();
+  uint64_t base = (uint64_t)set_of(page, d.sets) * d.ways;
+  uint64_t t = l < d.ways ? ld_rlx64(&d.tag[base + l]) : 0;
+  bool match = l < d.ways && tag_state(t) != ST_INVALID && tag_page(t) == page;
+  unsigned m = __ballot_sync(kFull, match);
+  if (!m) return P_MISS;
+  int w = __ffs(m) - 1;
+  line = (uint32_t)(base + w);
+  int pr = P_MISS;
+  if ((int)l == w) {
+    if (tag_state(t) == ST_BUSY) {
+      pr = P_BUSY;
+    } else {
+      uint64_t old = atomicAdd(&d.tag[line], PIN1);
+      uint64_t ost = tag_state(old);
+      if (tag_page(old) == page && (ost == ST_READY || ost == ST_MODIFIED)) {
+        if (!(old & TAG_REF)) atomicOr(&d.tag[line], TAG_REF);
+        fence_ar();  // the line data is read after the pin is observed
+        pr = P_HIT;
+      } else {
+        atomicAdd(&d.tag[line], (unsigned long long)(-(int64_t)PIN1));
+        pr = (ost == ST_BUSY && tag_page(old) == page) ? P_BUSY : P_MISS;
+      }
+    }
+  }
+  return __shfl_sync(kFull, pr, w);
+}
+
+// The warp needs one page pinned (uniform `page`): probe with a pin; on a miss the warp
+// issues and waits with nothing pinned, then probes again.  Returns the line in every
+// lane, or false on timeout/abort.  The caller unpins it (one unpin per pin).
 static __device__ bool warp_pin_page(const Dev &d, uint64_t page, uint32_t q0, uint64_t deadline,
                               uint32_t &line_out) {
   for (int round = 0;; ++round) {
     uint32_t line = 0;
-    int pr = P_MISS;
-    if (lane_id() == 0) pr = cache_probe(d, page, true, line);
-    pr = __shfl_sync(kFull, pr, 0);
+    int pr = warp_probe_pin(d, page, line);
     if (pr == P_HIT) {
-      line_out = __shfl_sync(kFull, line, 0);
+      line_out = line;
       if (lane_id() == 0 && round == 0) atomicAdd(&d.stats[S_HITS], 1ull);
       return true;
     }
@@ -695,8 +728,11 @@ __device__ __forceinline__ void complete_command(const Dev &d, uint32_t q, uint3
 
 // Alg. 1, warp-centric CQ polling of queue q: lane l checks entry offset+l of the
 // current 32-entry window against the expected phase; the mask accumulates found
-// entries; a full mask advances the head and rings the CQ doorbell.
-static __device__ __noinline__ bool cq_poll(const Dev &d, uint32_t q) {
+// entries (they may arrive in any order); a full mask advances the head and rings the
+// CQ doorbell.  The CQ has twice as many entries as the SQ, so with at most depth-1
+// commands outstanding and at most 31 consumed entries in the open window it never
+// fills (the device never has to wait for CQ space).
+static __device__ bool cq_poll(const Dev &d, uint32_t q) {
   unsigned l = lane_id();
   uint32_t *ps = &d.cq_poll[q * 4];
   uint32_t offset = ld_rlx32(&ps[0]), mask = ld_rlx32(&ps[1]), phase = ld_rlx32(&ps[2]);
@@ -704,7 +740,7 @@ static __device__ __noinline__ bool cq_poll(const Dev &d, uint32_t q) {
   for (int win = 0; win < 4; ++win) {
     bool valid = false;
     if (!((mask >> l) & 1u)) {
-      Cqe *c = &d.cq[(uint64_t)q * d.depth + offset + l];
+      Cqe *c = &d.cq[(uint64_t)q * d.cq_size + offset + l];
       uint32_t w3 = ld_acq32(&c->dw[3]);
       if (((w3 >> 16) & 1u) == phase) {
         complete_command(d, q, w3 & 0xFFFFu, w3 >> 17);
@@ -717,7 +753,7 @@ static __device__ __noinline__ bool cq_poll(const Dev &d, uint32_t q) {
     if (mask != kFull) break;
     mask = 0;
     offset += 32;
-    if (offset >= d.depth) {
+    if (offset >= d.cq_size) {
       offset = 0;
       phase ^= 1u;
     }
@@ -747,141 +783,194 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-// One step of the device behind queue q (warp-collective): read the SQ doorbell,
-// stamp newly visible commands with their arrival time, then in order execute every
-// command whose latency and the queue's throughput budget allow: copy the page
-// between the store (pinned host memory over the host link) and HBM, and post a CQE
-// {SQ head, SQ id, CID, status, phase}.
-static __device__ __noinline__ bool emu_step(const Dev &d, uint32_t q, uint32_t max_cmds) {
+// The emulated NVMe device.  Every service warp is one of its engines and may serve
+// any queue.  Per queue the device keeps (unwrapped counters): `fetch`, the next SQE to
+// take; `seen`, how far the doorbell has been observed (commands below it carry their
+// arrival time); `cqt`, the next CQ slot.  An engine takes up to kEmuBatch due commands
+// in SQ order by compare-and-swap on `fetch` (a command is due once its latency has
+// elapsed and the queue's throughput budget allows it), moves the pages between the
+// store (pinned host memory, over the host link) and HBM, then reserves CQ slots and
+// posts the CQEs {SQ head, SQ id, CID, status, phase}.  Commands of one queue complete
+// in any order, as NVMe allows.
+constexpr uint32_t kEmuBatch = 2;
+
+static __device__ uint32_t emu_serve(const Dev &d, uint32_t q) {
   unsigned l = lane_id();
   uint32_t *es = &d.emu[q * 4];
-  uint32_t head = 0, ctail = 0, phase = 0, db = 0;
+  uint32_t f = 0, k = 0;
   uint64_t now = gtimer();
   if (l == 0) {
-    head = ld_rlx32(&es[0]);
-    ctail = ld_rlx32(&es[1]);
-    phase = ld_rlx32(&es[2]);
-    uint32_t seen = ld_rlx32(&es[3]);
-    db = ld_acq32(&d.sq_db[q]);
-    while (seen != db) {
-      st_rlx64(&d.emu_arrival[(uint64_t)q * d.depth + seen], now);
-      seen = (seen + 1) & d.dmask;
+    // `seen` must be read before the doorbell: it only ever takes doorbell values read
+    // earlier, so seen <= tail here and (db - seen) mod depth is the exact number of
+    // newly exposed commands (never a wrapped-around difference)
+    uint32_t seen = ld_acq32(&es[1]);
+    uint32_t db = ld_acq32(&d.sq_db[q]);
+    // stamp the arrival of commands the doorbell has newly exposed, then publish them
+    uint32_t fresh = (db - (seen & d.dmask)) & d.dmask;
+    if (fresh) {
+      for (uint32_t i = 0; i < fresh; ++i)
+        st_rlx64(&d.emu_arrival[(uint64_t)q * d.depth + ((seen + i) & d.dmask)], now);
+      fence_ar();
+      atomicCAS(&es[1], seen, seen + fresh);
+      seen = ld_acq32(&es[1]);
     }
-    st_rlx32(&es[3], seen);
-  }
-  head = __shfl_sync(kFull, head, 0);
-  ctail = __shfl_sync(kFull, ctail, 0);
-  phase = __shfl_sync(kFull, phase, 0);
-  db = __shfl_sync(kFull, db, 0);
-  uint32_t done = 0;
-  uint64_t busy = 0;
-  if (l == 0) busy = ld_rlx64(&d.emu_busy[q]);
-  while (head != db && done < max_cmds) {
-    uint64_t i = (uint64_t)q * d.depth + head;
-    int go = 0;
-    uint32_t dw0 = 0, nlb = 0;
-    uint64_t prp1 = 0, slba = 0;
-    if (l == 0) {
-      uint64_t arr = ld_rlx64(&d.emu_arrival[i]);
-      uint64_t start = arr + d.lat_ns;
-      if (busy > start) start = busy;
-      go = now >= start;
-      if (go && ((ctail + 1) & d.dmask) == ld_acq32(&d.cq_db[q])) go = 0;  // CQ full
-      if (go) {
-        const uint32_t *e = d.sq[i].dw;
-        int4 a = ld_cg16(e), b = ld_cg16(e + 4), c = ld_cg16(e + 8), f = ld_cg16(e + 12);
-        dw0 = (uint32_t)a.x;
-        prp1 = (uint64_t)(uint32_t)b.z | ((uint64_t)(uint32_t)b.w << 32);
-        slba = (uint64_t)(uint32_t)c.z | ((uint64_t)(uint32_t)c.w << 32);
-        nlb = (uint32_t)f.x & 0xFFFFu;
-        busy = start + d.ns_per_page * (((uint64_t)nlb + 1) * 512 / kPage);
+    f = ld_rlx32(&es[0]);
+    uint32_t avail = seen - f;
+    if ((int32_t)avail > 0) {
+      if (avail > kEmuBatch) avail = kEmuBatch;
+      while (k < avail) {
+        uint64_t arr = ld_rlx64(&d.emu_arrival[(uint64_t)q * d.depth + ((f + k) & d.dmask)]);
+        if (now < arr + d.lat_ns) break;
+        ++k;
       }
+      if (k && d.ns_per_page) {
+        uint64_t busy = ld_rlx64(&d.emu_busy[q]);
+        if (busy > now) {
+          k = 0;
+        } else {
+          uint64_t nb = now + d.ns_per_page * k;
+          if (atomicCAS(&d.emu_busy[q], (unsigned long long)busy, (unsigned long long)nb) != busy) k = 0;
+        }
+      }
+      if (k && atomicCAS(&es[0], f, f + k) != f) k = 0;
     }
-    go = __shfl_sync(kFull, go, 0);
-    if (!go) break;
-    dw0 = __shfl_sync(kFull, dw0, 0);
-    prp1 = __shfl_sync(kFull, prp1, 0);
-    slba = __shfl_sync(kFull, slba, 0);
-    nlb = __shfl_sync(kFull, nlb, 0);
-    uint32_t opcode = dw0 & 0xFFu, cid = dw0 >> 16;
+  }
+  k = __shfl_sync(kFull, k, 0);
+  if (!k) return 0;
+  f = __shfl_sync(kFull, f, 0);
+  // command fields: lane i < k reads SQE f+i
+  uint32_t dw0 = 0, nlb = 0, status = 0;
+  uint64_t prp1 = 0, slba = 0;
+  bool drop = false;
+  if (l < k) {
+    uint64_t i = (uint64_t)q * d.depth + ((f + l) & d.dmask);
+    const uint32_t *e = d.sq[i].dw;
+    int4 a = ld_cg16(e), b = ld_cg16(e + 4), c = ld_cg16(e + 8), g = ld_cg16(e + 12);
+    dw0 = (uint32_t)a.x;
+    prp1 = (uint64_t)(uint32_t)b.z | ((uint64_t)(uint32_t)b.w << 32);
+    slba = (uint64_t)(uint32_t)c.z | ((uint64_t)(uint32_t)c.w << 32);
+    nlb = (uint32_t)g.x & 0xFFFFu;
+    uint32_t opcode = dw0 & 0xFFu;
     uint64_t nbytes = ((uint64_t)nlb + 1) * 512;
-    uint64_t off = slba * 512;
-    uint32_t status = 0;
-    bool drop = false;
+    if (opcode != OP_FLUSH && (slba * 512 + nbytes > d.store_bytes || nbytes != kPage)) status = 0x80;
     if (d.fault_flags) {
-      uint64_t h = mix64(d.seed ^ ((uint64_t)q << 40) ^ ((uint64_t)ld_rlx64(&d.sqe_state[i]) >> 2));
+      uint64_t h = mix64(d.seed ^ ((uint64_t)q << 40) ^ (uint64_t)(f + l));
       if ((uint32_t)(h >> 32) < d.fault_thresh) {
-        if (d.fault_flags & 1u) status = 0x6;        // internal error
+        if (d.fault_flags & 1u) status = 0x6;
         if (d.fault_flags & 2u) drop = true;
       }
     }
-    if (opcode != OP_FLUSH && (off + nbytes > d.store_bytes || nbytes != kPage)) status = 0x80;  // LBA out of range
-    if (status == 0 && opcode == OP_READ) {
-      warp_copy_page((void *)prp1, d.store + off);
-      if (l == 0) atomicAdd(&d.stats[S_BYTES_READ], (unsigned long long)nbytes);
-    } else if (status == 0 && opcode == OP_WRITE) {
-      warp_copy_page(d.store + off, (const void *)prp1);
-      if (l == 0) atomicAdd(&d.stats[S_BYTES_WRITTEN], (unsigned long long)nbytes);
+  }
+  // data movement: every page of the batch has its loads in flight before any store
+  int4 v[kEmuBatch][8];
+  uint64_t srcs[kEmuBatch], dsts[kEmuBatch];
+  bool mv[kEmuBatch];
+#pragma unroll
+  for (uint32_t j = 0; j < kEmuBatch; ++j) {
+    uint32_t opj = __shfl_sync(kFull, dw0, j) & 0xFFu;
+    uint32_t stj = __shfl_sync(kFull, status, j);
+    uint64_t pj = __shfl_sync(kFull, prp1, j), sj = __shfl_sync(kFull, slba, j);
+    mv[j] = j < k && stj == 0 && (opj == OP_READ || opj == OP_WRITE);
+    srcs[j] = opj == OP_READ ? (uint64_t)(d.store + sj * 512) : pj;
+    dsts[j] = opj == OP_READ ? pj : (uint64_t)(d.store + sj * 512);
+    if (mv[j]) {
+      const int4 *sp = (const int4 *)srcs[j];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) v[j][t] = ld_cg16(sp + t * 32 + l);
     }
-    __threadfence_system();
-    __syncwarp();
-    head = (head + 1) & d.dmask;
-    if (l == 0) {
-      atomicAdd(&d.stats[S_COMMANDS], 1ull);
-      if (!drop) {
-        Cqe *c = &d.cq[(uint64_t)q * d.depth + ctail];
-        st_rlx32(&c->dw[0], 0u);
-        st_rlx32(&c->dw[1], 0u);
-        st_rlx32(&c->dw[2], (q << 16) | head);
-        fence_ar();
-        st_rel32(&c->dw[3], cid | (phase << 16) | (status << 17));
-        ctail = (ctail + 1) & d.dmask;
-        if (ctail == 0) phase ^= 1u;
-      }
+  }
+  uint32_t rd = 0, wr = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < kEmuBatch; ++j) {
+    if (mv[j]) {
+      int4 *dp = (int4 *)dsts[j];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) st_cg16(dp + t * 32 + l, v[j][t]);
+      if ((__shfl_sync(kFull, dw0, j) & 0xFFu) == OP_READ) ++rd;
+      else ++wr;
     }
-    ctail = __shfl_sync(kFull, ctail, 0);
-    phase = __shfl_sync(kFull, phase, 0);
-    ++done;
+  }
+  __threadfence();
+  __syncwarp();
+  // completion entries
+  uint32_t slot0 = 0;
+  if (l == 0) slot0 = atomicAdd(&es[2], k);
+  slot0 = __shfl_sync(kFull, slot0, 0);
+  if (l < k) {
+    uint32_t sl = slot0 + l;
+    uint32_t pos = sl % d.cq_size;
+    uint32_t phase = ((sl / d.cq_size) & 1u) ^ 1u;
+    Cqe *c = &d.cq[(uint64_t)q * d.cq_size + pos];
+    uint32_t cid = dw0 >> 16;
+    if (drop) {
+      // the completion is lost; leave a harmless entry with the old phase
+      st_rlx32(&c->dw[2], (q << 16) | ((f + l + 1) & d.dmask));
+    } else {
+      st_rlx32(&c->dw[0], 0u);
+      st_rlx32(&c->dw[1], 0u);
+      st_rlx32(&c->dw[2], (q << 16) | ((f + l + 1) & d.dmask));
+      fence_ar();
+      st_rel32(&c->dw[3], cid | (phase << 16) | (status << 17));
+    }
   }
   if (l == 0) {
-    st_rlx32(&es[0], head);
-    st_rlx32(&es[1], ctail);
-    st_rlx32(&es[2], phase);
-    st_rlx64(&d.emu_busy[q], busy);
+    atomicAdd(&d.stats[S_COMMANDS], (unsigned long long)k);
+    if (rd) atomicAdd(&d.stats[S_BYTES_READ], (unsigned long long)rd * kPage);
+    if (wr) atomicAdd(&d.stats[S_BYTES_WRITTEN], (unsigned long long)wr * kPage);
   }
-  return done != 0;
+  __syncwarp();
+  return k;
 }
 
 // ================================================================ engine
 // One cooperative launch per library call.  Warp 0 of every CTA is a service warp:
-// it is the emulated device and the CQ poller for queues q = cta, cta + grid, ...
-// The other warps run the application.  No kernel of the library ever waits on
-// another launch: the device, the pollers and the waiters are co-resident warps of
-// one grid, and every wait is bounded by a deadline.
-static __device__ __noinline__ void service_loop(const Dev &d, uint32_t n_app, uint64_t deadline) {
+// an engine of the emulated device for every queue, and the Alg. 1 poller of queues
+// q = cta, cta + grid, ...  The other warps run the application.  No kernel of the
+// library ever waits on another launch: the device, the pollers and the waiters are
+// co-resident warps of one grid, and every wait is bounded by a deadline.
+static __device__ void service_loop(const Dev &d, uint32_t n_app, uint64_t deadline) {
   uint32_t sw = blockIdx.x, nsw = gridDim.x;
+  unsigned l = lane_id();
   uint32_t ns = 32;
+  uint32_t start = (uint32_t)(((uint64_t)sw * 32) % d.Q);
   for (;;) {
     bool progress = false;
-    for (uint32_t q = sw; q < d.Q; q += nsw) {
-      progress |= emu_step(d, q, 8);
-      progress |= cq_poll(d, q);
+    // device engine: look at 32 queues per step, one per lane
+    for (uint32_t base = 0; base < d.Q; base += 32) {
+      uint32_t qi = start + base + l;
+      uint32_t q = qi % d.Q;
+      bool has = false;
+      if (base + l < d.Q) {
+        uint32_t *es = &d.emu[q * 4];
+        uint32_t db = ld_acq32(&d.sq_db[q]);
+        uint32_t f = ld_rlx32(&es[0]);
+        has = ((db - (f & d.dmask)) & d.dmask) != 0;
+      }
+      unsigned m = __ballot_sync(kFull, has);
+      while (m) {
+        int j = __ffs(m) - 1;
+        m &= m - 1;
+        uint32_t qj = __shfl_sync(kFull, q, j);
+        if (emu_serve(d, qj)) progress = true;
+      }
     }
+    // completion side (Alg. 1) for the queues this warp polls
+    for (uint32_t q = sw; q < d.Q; q += nsw) progress |= cq_poll(d, q);
     if (progress) {
       ns = 32;
       continue;
     }
     uint32_t done = 0;
-    if (lane_id() == 0) done = ld_acq32(&d.run->app_done);
+    if (l == 0) done = ld_acq32(&d.run->app_done);
     done = __shfl_sync(kFull, done, 0);
     if (done >= n_app) {
       bool drained = true;
-      for (uint32_t q = sw; q < d.Q; q += nsw)
+      for (uint32_t q = l; q < d.Q; q += 32)
         if ((ld_acq64(&d.sq_resv[q]) >> 32) != 0) drained = false;
       if (__all_sync(kFull, drained)) break;
     }
     if (gtimer() > deadline) {
-      if (lane_id() == 0) set_error(d, -110);
+      if (l == 0) set_error(d, -110);
       break;
     }
     __nanosleep(ns);
@@ -927,7 +1016,7 @@ struct AppCtx {
 };
 
 template <class App>
-__global__ void __launch_bounds__(kThreads) engine_kernel(Dev d, App app) {
+__global__ void __launch_bounds__(kThreads, 2) engine_kernel(Dev d, App app) {
   uint32_t warp = threadIdx.x >> 5;
   uint32_t n_app = gridDim.x * (kWarps - 1);
   uint64_t deadline = gtimer() + d.timeout_ns;
@@ -937,8 +1026,15 @@ __global__ void __launch_bounds__(kThreads) engine_kernel(Dev d, App app) {
   }
   AppCtx a;
   a.warp = blockIdx.x * (kWarps - 1) + (warp - 1);
-  a.n_warps = n_app;
-  a.q0 = (uint32_t)(((uint64_t)a.warp * 32 + lane_id()) % d.Q);
+  a.n_warps = (d.app_active && d.app_active < n_app) ? d.app_active : n_app;
+  if (a.warp >= a.n_warps) {
+    // not needed by this call: keeps the working set of the active warps in the cache
+    if (lane_id() == 0) atomicAdd(&d.run->app_done, 1u);
+    return;
+  }
+  // home queue by thread index, spread so that the lanes of a warp and the lane 0 of
+  // consecutive warps all start on different queues
+  a.q0 = (uint32_t)((a.warp + (uint64_t)lane_id() * ((d.Q + 31) / 32)) % d.Q);
   a.deadline = deadline;
   app.run(d, a);
   __syncwarp();

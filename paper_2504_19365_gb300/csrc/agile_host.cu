@@ -462,7 +462,8 @@ int agile_init(const agile_config *cfg_in, agile_ctx **out) {
   d.sh_key = (unsigned long long *)A((uint64_t)buckets * 4 * 8);
   d.sh_val = (unsigned long long *)A((uint64_t)buckets * 4 * 8);
   d.sq = (Sqe *)A(Q * D * sizeof(Sqe));
-  d.cq = (Cqe *)A(Q * D * sizeof(Cqe));
+  d.cq_size = 2 * dep;
+  d.cq = (Cqe *)A(Q * 2 * D * sizeof(Cqe));
   d.sqe_state = (unsigned long long *)A(Q * D * 8);
   d.cmd_ctx = (unsigned long long *)A(Q * D * 8);
   d.cmpl = (unsigned long long *)A(Q * D * 8);
@@ -487,8 +488,7 @@ int agile_init(const agile_config *cfg_in, agile_ctx **out) {
   {
     std::vector<uint32_t> init(Q * 4, 0);
     for (uint64_t q = 0; q < Q; ++q) init[q * 4 + 2] = 1;
-    if (cudaMemcpy(d.cq_poll, init.data(), Q * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(d.emu, init.data(), Q * 16, cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (cudaMemcpy(d.cq_poll, init.data(), Q * 16, cudaMemcpyHostToDevice) != cudaSuccess) {
       agile_destroy(c);
       return AGILE_ECUDA;
     }
@@ -521,6 +521,7 @@ int agile_destroy(agile_ctx *c) {
     cudaDeviceSynchronize();
   }
   for (void *p : c->dallocs) cudaFree(p);
+  if (c->bfs_hubq) cudaFree(c->bfs_hubq);
   if (c->store_host) cudaFreeHost(c->store_host);
   delete c;
   return AGILE_OK;
@@ -567,14 +568,14 @@ int agile_read_async(agile_ctx *c, const uint64_t *d_pages, uint32_t n, void *d_
   if (((uintptr_t)d_dst) & 15) return AGILE_EINVAL;
   if (n == 0) return AGILE_OK;
   ReadApp app{d_pages, n, (uint8_t *)d_dst, d_tok, mode, 0};
-  return launch_engine(c, app, stream);
+  return launch_engine(c, app, stream, warps_for_cache(c, mode == AGILE_ASYNC ? 48 : 4, 8));
 }
 
 int agile_prefetch(agile_ctx *c, const uint64_t *d_pages, uint32_t n, void *stream) {
   if (!c || (n && !d_pages)) return AGILE_EINVAL;
   if (n == 0) return AGILE_OK;
   ReadApp app{d_pages, n, nullptr, nullptr, AGILE_ASYNC, 1};
-  return launch_engine(c, app, stream);
+  return launch_engine(c, app, stream, warps_for_cache(c, 48, 8));
 }
 
 int agile_write_async(agile_ctx *c, const uint64_t *d_pages, uint32_t n, const void *d_src, agile_token *d_tok,
@@ -583,7 +584,7 @@ int agile_write_async(agile_ctx *c, const uint64_t *d_pages, uint32_t n, const v
   if (((uintptr_t)d_src) & 15) return AGILE_EINVAL;
   if (n == 0) return AGILE_OK;
   WriteApp app{d_pages, n, (const uint8_t *)d_src, d_tok};
-  return launch_engine(c, app, stream);
+  return launch_engine(c, app, stream, warps_for_cache(c, 4, 8));
 }
 
 int agile_wait(agile_ctx *c, const agile_token *d_tok, uint32_t n, int32_t *d_status, void *stream) {

@@ -136,7 +136,9 @@ def csr_from_edges(n: int, src: np.ndarray, dst: np.ndarray, symmetrize: bool = 
     if symmetrize:
         src, dst = np.concatenate([src, dst]), np.concatenate([dst, src])
     keep = src != dst
-    key = np.unique(src[keep] * np.int64(n) + dst[keep])
+    key = np.sort(src[keep] * np.int64(n) + dst[keep])
+    if key.size:
+        key = key[np.concatenate([[True], key[1:] != key[:-1]])]
     s = key // n
     d = (key % n).astype(np.int32)
     deg = np.bincount(s, minlength=n).astype(np.int64)
@@ -148,19 +150,28 @@ def csr_from_edges(n: int, src: np.ndarray, dst: np.ndarray, symmetrize: bool = 
 def rmat_edges(seed: int, scale: int, edge_factor: int, a=0.57, b=0.19, c=0.19):
     """R-MAT edge list (Chakrabarti, Zhan, Faloutsos, SDM 2004): for each edge and each of
     ``scale`` bit levels one uniform draw picks a quadrant with probabilities
-    (a, b, c, 1 - a - b - c); no vertex relabelling."""
+    (a, b, c, 1 - a - b - c); no vertex relabelling.  Each draw is a 16-bit field of a
+    SplitMix64 output (four levels per output), compared with the thresholds scaled
+    to 2^16."""
     m = edge_factor << scale
     src = np.zeros(m, dtype=np.int64)
     dst = np.zeros(m, dtype=np.int64)
-    ab = a + b
-    abc = a + b + c
-    for lvl in range(scale):
-        u = uniform01(seed, m, offset=lvl * m)
-        bit = np.int64(1) << np.int64(scale - 1 - lvl)
-        right = ((u >= a) & (u < ab)) | (u >= abc)   # quadrants b and d set the dst bit
-        down = u >= ab                                # quadrants c and d set the src bit
-        src |= np.where(down, bit, np.int64(0))
-        dst |= np.where(right, bit, np.int64(0))
+    ta = np.uint64(round(a * 65536))
+    tab = np.uint64(round((a + b) * 65536))
+    tabc = np.uint64(round((a + b + c) * 65536))
+    edges = np.arange(m, dtype=np.uint64)
+    for blk in range((scale + 3) // 4):
+        u = splitmix64(seed, edges + np.uint64(blk * m))
+        for k in range(4):
+            lvl = blk * 4 + k
+            if lvl >= scale:
+                break
+            x = (u >> np.uint64(16 * k)) & np.uint64(0xFFFF)
+            sh = np.int64(scale - 1 - lvl)
+            right = ((x >= ta) & (x < tab)) | (x >= tabc)   # quadrants b and d set the dst bit
+            down = x >= tab                                  # quadrants c and d set the src bit
+            src |= down.astype(np.int64) << sh
+            dst |= right.astype(np.int64) << sh
     return src, dst
 
 
