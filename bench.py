@@ -36,6 +36,7 @@ import synth  # noqa: E402
 
 METRIC_BFS = "BFS edges/s (async), RMAT scale 20 through a 1/8 HBM cache"
 METRIC_EMB = "embedding-bag lookups/s (async), 65,536x128 FP32 table through a 4 MiB cache"
+EMB_WORKLOAD = "65,536x128 FP32 table, 4 MiB 8-way cache, 16 batches x 256 bags x 16 uniform indices"
 PAGE = 4096
 
 
@@ -125,6 +126,19 @@ class Clocks:
 
 # ============================================================================ reference arm
 
+def bfs_config(n, cols, srcs, cache_bytes, ways=8, queues=128, depth=256):
+    return {"workload": "bfs_rmat20_ef16_cache1/8",
+            "graph": {"vertices": int(n), "csr_entries": int(cols.size), "a": 0.57, "b": 0.19, "c": 0.19, "seed": 3},
+            "sources": [int(s) for s in srcs], "cache_bytes": int(cache_bytes), "ways": ways, "queues": queues,
+            "depth": depth, "emulated_device": "pinned host memory, no latency model",
+            "l2": "flushed (256 MiB write) and HBM cache invalidated before every BFS, untimed"}
+
+
+def bfs_cache_bytes(cols, ways=8):
+    lines = max(ways, (cols.nbytes // 8 + PAGE - 1) // PAGE)
+    return (lines + ways - 1) // ways * ways * PAGE
+
+
 def run_reference(args):
     """The CPU oracle, as it stands, on the host cores: the same workload, each step a
     bounded sample of it."""
@@ -142,6 +156,8 @@ def run_reference(args):
                 e += oracle.bfs(off, cols, int(s))[1]
             return e
         unit, metric, sample = "edges/s", METRIC_BFS, "8 BFS from the seeded sources over the full graph"
+        config = bfs_config(n, cols, srcs, bfs_cache_bytes(cols))
+        dtype = "int32"
     else:
         rows, dim = 65536, 128
         T = synth.table_normal(1, rows, dim)
@@ -153,6 +169,8 @@ def run_reference(args):
                 oracle.embedding_bag(T, idx[b], off)
             return 16 * 4096
         unit, metric, sample = "lookups/s", METRIC_EMB, "16 batches x 256 bags x 16 indices"
+        config = {"workload": EMB_WORKLOAD}
+        dtype = "f32"
     for _ in range(args.warmup):
         step()
     t0 = time.perf_counter()
@@ -163,8 +181,8 @@ def run_reference(args):
     v = work / dt
     line = {"impl": "reference", "metric": metric, "value": v, "unit": unit, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": {"workload": args.workload},
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic", "config": config,
             "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -212,10 +230,10 @@ def run_bfs(args, torch, ag, dev, rank, world):
     col0 = round_page(off.nbytes)
     total = col0 + round_page(cols.nbytes)
     ways = 8
-    lines = max(ways, (cols.nbytes // 8 + PAGE - 1) // PAGE)
-    cache_bytes = (lines + ways - 1) // ways * ways * PAGE
+    cache_bytes = bfs_cache_bytes(cols, ways)
     cfg = ag.agile_config_default(store_bytes=total, cache_bytes=cache_bytes, ways=ways,
-                                  device=torch.cuda.current_device())
+                                  device=torch.cuda.current_device(),
+                                  wait_timeout_ns=int(args.wait_timeout_s * 1e9))
     ctx = ag.agile_init(cfg)
     stream = torch.cuda.current_stream().cuda_stream
     ag.agile_store_write(ctx, 0, off.ctypes.data, off.nbytes)
@@ -305,12 +323,8 @@ def run_bfs(args, torch, ag, dev, rank, world):
         "ms_per_step": ms_async / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic",
-        "config": {"workload": "bfs_rmat20_ef16_cache1/8", "graph": {"vertices": n, "csr_entries": int(cols.size),
-                   "a": 0.57, "b": 0.19, "c": 0.19, "seed": 3}, "sources": [int(s) for s in srcs],
-                   "cache_bytes": cache_bytes, "ways": ways, "queues": cfg.num_queues, "depth": cfg.queue_depth,
-                   "emulated_device": "pinned host memory, no latency model", "ctas": ctas,
-                   "l2": "flushed (256 MiB write) and HBM cache invalidated before every BFS, untimed",
-                   "parallelism": f"replicas x{world}"},
+        "config": dict(bfs_config(n, cols, srcs, cache_bytes, ways, cfg.num_queues, cfg.queue_depth),
+                       ctas=ctas, parallelism=f"replicas x{world}"),
         "sync": {"value": work_sync / (ms_sync * 1e-3), "unit": "edges/s", "ms_per_step": ms_sync / args.steps},
         "async_over_sync": ms_sync / ms_async,
         "roofline": {"bound": "host_link", "achieved": achieved, "peak": link_peak, "unit": "GB/s",
@@ -339,7 +353,8 @@ def run_embedding(args, torch, ag, dev, rank, world):
     off = synth.bags_fixed(nb, pool)
     idx = np.concatenate([synth.indices_uniform(2, nb * pool, rows, offset=b * nb * pool) for b in range(batches)])
     cfg = ag.agile_config_default(store_bytes=T.nbytes, cache_bytes=4 << 20, ways=8,
-                                  device=torch.cuda.current_device())
+                                  device=torch.cuda.current_device(),
+                                  wait_timeout_ns=int(args.wait_timeout_s * 1e9))
     ctx = ag.agile_init(cfg)
     stream = torch.cuda.current_stream().cuda_stream
     ag.agile_store_write(ctx, 0, T.ctypes.data, T.nbytes)
@@ -372,7 +387,7 @@ def run_embedding(args, torch, ag, dev, rank, world):
     look = batches * nb * pool * args.steps
     return {"async": look / (ms_a * 1e-3), "sync": look / (ms_s * 1e-3), "unit": "lookups/s",
             "ms_per_step_async": ms_a / args.steps, "ms_per_step_sync": ms_s / args.steps,
-            "workload": "65,536x128 FP32 table, 4 MiB 8-way cache, 16 batches x 256 bags x 16 uniform indices"}
+            "workload": EMB_WORKLOAD}
 
 
 def main():
@@ -384,6 +399,8 @@ def main():
     ap.add_argument("--workload", default="bfs", choices=["bfs", "embedding"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--wait-timeout-s", type=float, default=10.0,
+                    help="bound on every wait inside a library call (raise it under a profiler)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

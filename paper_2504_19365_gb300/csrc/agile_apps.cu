@@ -21,10 +21,12 @@ constexpr int kMaxF4 = 8;  // float4 columns per lane: dim <= 32 * 4 * 8 = 1024
 // held across a wait (Sec. 2.3.2).
 //   SYNC : each row's page is requested when the row is needed; a miss stalls the warp
 //          until it is filled (issue then stall, Sec. 4.4 "AGILE sync").
-//   ASYNC: pages are requested a group ahead (the next 32 indices of this bag, or the
-//          first 32 of the warp's next bag): the warp issues them, continues with the
-//          rows of the current group and only waits if a row's page is still in flight
-//          when it gets there (Sec. 4.4 "AGILE async": prefetch the next epoch).
+//   ASYNC: the warp walks its bags as one stream of rows and keeps the pages of the
+//          next `ahead` rows requested: it issues them, continues with the current
+//          rows and only waits if a row's page is still in flight when it gets there
+//          (Sec. 4.4 "AGILE async": prefetch ahead of the computation).  `ahead` is
+//          sized from the cache so that rows requested ahead are not evicted before
+//          they are used.
 struct EmbApp {
   uint64_t page0;  // first store page of the table
   uint32_t rows, dim;
@@ -33,49 +35,62 @@ struct EmbApp {
   uint32_t n_bags;
   float *out;
   uint32_t mode;
+  uint32_t ahead;  // rows requested ahead of the one being summed (ASYNC), 1..32
 
   __device__ __forceinline__ uint64_t row_page(uint64_t r) const { return page0 + (r * dim * 4) / kPage; }
 
-  // issue (without waiting) the pages of indices [i0, min(i0+32, e))
-  __device__ bool prefetch_group(const Dev &d, const AppCtx &a, int64_t i0, int64_t e) const {
-    unsigned l = lane_id();
-    int64_t i = i0 + l;
-    bool want = i < e;
-    uint64_t r = want ? (uint64_t)idx[i] : 0;
-    if (want && r >= rows) {
-      set_error(d, AGILE_EINVAL);
-      want = false;
+  // position in the warp's stream of rows: bag b, index i
+  struct Cursor {
+    uint32_t b;
+    int64_t i, e;
+  };
+  __device__ __forceinline__ void cur_init(const AppCtx &a, Cursor &c) const {
+    c.b = a.warp;
+    c.i = c.b < n_bags ? off[c.b] : 0;
+    c.e = c.b < n_bags ? off[c.b + 1] : 0;
+    skip_empty(a, c);
+  }
+  __device__ __forceinline__ void skip_empty(const AppCtx &a, Cursor &c) const {
+    while (c.b < n_bags && c.i >= c.e) {
+      c.b += a.n_warps;
+      if (c.b < n_bags) {
+        c.i = off[c.b];
+        c.e = off[c.b + 1];
+      }
     }
-    return warp_request(d, want, row_page(r), a.q0, false, a.deadline);
+  }
+  // issue the pages of the next `cnt` rows of the stream from cursor c (advances c)
+  __device__ bool issue_rows(const Dev &d, const AppCtx &a, Cursor &c, uint32_t cnt) const {
+    while (cnt && c.b < n_bags) {
+      uint32_t take = (uint32_t)min((int64_t)cnt, c.e - c.i);
+      unsigned l = lane_id();
+      bool want = l < take;
+      uint64_t r = want ? (uint64_t)idx[c.i + l] : 0;
+      if (want && r >= rows) {
+        set_error(d, AGILE_EINVAL);
+        want = false;
+      }
+      if (!warp_request(d, want, row_page(r), a.q0, false, a.deadline)) return false;
+      c.i += take;
+      cnt -= take;
+      skip_empty(a, c);
+    }
+    return true;
   }
 
   __device__ void run(const Dev &d, const AppCtx &a) const {
     unsigned l = lane_id();
     const uint32_t nf4 = dim / 4;
     const bool async = mode == AGILE_ASYNC;
-    uint32_t b = a.warp;
-    if (b >= n_bags) return;
-    int64_t s = off[b], e = off[b + 1];
-    if (async && s < e && !prefetch_group(d, a, s, e)) return;
-    for (; b < n_bags; b += a.n_warps) {
-      s = off[b];
-      e = off[b + 1];
+    Cursor pf;  // prefetch cursor, `ahead` rows in front of the summation
+    cur_init(a, pf);
+    if (async && !issue_rows(d, a, pf, ahead)) return;
+    for (uint32_t b = a.warp; b < n_bags; b += a.n_warps) {
+      int64_t s = off[b], e = off[b + 1];
       float4 acc[kMaxF4];
 #pragma unroll
       for (int k = 0; k < kMaxF4; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
       for (int64_t i0 = s; i0 < e; i0 += 32) {
-        // lookahead: the next group of this bag, else the first group of the next bag
-        if (async) {
-          if (i0 + 32 < e) {
-            if (!prefetch_group(d, a, i0 + 32, e)) return;
-          } else {
-            uint64_t nb = (uint64_t)b + a.n_warps;
-            if (nb < n_bags) {
-              int64_t ns = off[nb], ne = off[nb + 1];
-              if (ns < ne && !prefetch_group(d, a, ns, ne)) return;
-            }
-          }
-        }
         int64_t i = i0 + l;
         uint64_t r = i < e ? (uint64_t)idx[i] : 0;
         if (i < e && r >= rows) {
@@ -84,6 +99,7 @@ struct EmbApp {
         }
         uint32_t cnt = (uint32_t)min((int64_t)32, e - i0);
         for (uint32_t j = 0; j < cnt; ++j) {
+          if (async && !issue_rows(d, a, pf, 1)) return;
           uint64_t rj = __shfl_sync(kFull, r, j);
           uint64_t byte = rj * dim * 4;
           uint64_t pg = page0 + byte / kPage;
@@ -280,46 +296,60 @@ struct BfsApp {
     return true;
   }
 
-  // take slices of the queued long lists of level L until none is left
+  // Take slices of the queued long lists of level L until none is left.  All warps work
+  // on the first list that still has slices (a shared cursor moves past exhausted
+  // lists), so a helper never walks the whole queue.  Lists queued after this warp
+  // leaves are sliced by the warps that queued them, which run this same loop.
   __device__ bool help_hubs(const Dev &d, const AppCtx &a, int32_t L, uint32_t &found, Pin &pc) const {
     unsigned l = lane_id();
     uint32_t ns = 64;
     for (;;) {
-      uint32_t c = 0;
-      if (l == 0) c = ld_acq32(&d.run->hub_count[L & 1]);
-      c = min(__shfl_sync(kFull, c, 0), hub_cap);
-      bool pending = false;
-      for (uint32_t i = 0; i < c; ++i) {
-        HubEntry *h = &hubq[i];
-        uint32_t rd = 0;
-        if (l == 0) rd = ld_acq32(&h->ready);
-        rd = __shfl_sync(kFull, rd, 0);
-        if (rd != (uint32_t)L + 1) {
-          pending = true;
-          continue;
-        }
-        int64_t s = ld_cg_s64(&h->s), e = ld_cg_s64(&h->e);
-        uint32_t slices = (uint32_t)((e - s + kSlice - 1) / kSlice);
-        for (;;) {
-          uint32_t k = 0;
-          if (l == 0) k = atomicAdd(&h->next, 1u);
-          k = __shfl_sync(kFull, k, 0);
-          if (k >= slices) break;
-          int64_t p0 = s + (int64_t)k * kSlice, p1 = min(e, p0 + (int64_t)kSlice);
-          for (int64_t pos = p0 + l; pos - l < p1; pos += 32) {
-            bool act = pos < p1;
-            int32_t u = 0;
-            if (!gather<int32_t>(d, a, col_page0, act, (uint64_t)(act ? pos : p0) * 4, u, pc)) return false;
-            visit(act, u, L, found);
+      uint32_t c = 0, i = 0, rd = 0, k = 0;
+      int64_t s = 0, e = 0;
+      int act = 0;  // 0 done, 1 slice claimed, 2 retry
+      if (l == 0) {
+        c = min(ld_acq32(&d.run->hub_count[L & 1]), hub_cap);
+        i = ld_acq32(&d.run->hub_cursor[L & 1]);
+        if (i < c) {
+          HubEntry *h = &hubq[i];
+          rd = ld_acq32(&h->ready);
+          if (rd != (uint32_t)L + 1) {
+            act = 2;  // queued, not yet published
+          } else {
+            s = ld_cg_s64(&h->s);
+            e = ld_cg_s64(&h->e);
+            uint32_t slices = (uint32_t)((e - s + kSlice - 1) / kSlice);
+            k = atomicAdd(&h->next, 1u);
+            if (k < slices) {
+              act = 1;
+            } else {
+              atomicCAS(&d.run->hub_cursor[L & 1], i, i + 1);
+              act = 3;  // exhausted: look again at once
+            }
           }
         }
       }
-      if (!pending) return true;
-      if (gtimer() > a.deadline || aborted(d)) {
-        if (l == 0) set_error(d, -110);
-        return false;
+      act = __shfl_sync(kFull, act, 0);
+      if (act == 0) return true;
+      if (act == 3) continue;
+      if (act == 2) {
+        if (gtimer() > a.deadline || aborted(d)) {
+          if (l == 0) set_error(d, -110);
+          return false;
+        }
+        backoff(ns);
+        continue;
       }
-      backoff(ns);
+      s = __shfl_sync(kFull, s, 0);
+      e = __shfl_sync(kFull, e, 0);
+      k = __shfl_sync(kFull, k, 0);
+      int64_t p0 = s + (int64_t)k * kSlice, p1 = min(e, p0 + (int64_t)kSlice);
+      for (int64_t pos = p0 + l; pos - l < p1; pos += 32) {
+        bool on = pos < p1;
+        int32_t u = 0;
+        if (!gather<int32_t>(d, a, col_page0, on, (uint64_t)(on ? pos : p0) * 4, u, pc)) return false;
+        visit(on, u, L, found);
+      }
     }
   }
 
@@ -334,6 +364,7 @@ struct BfsApp {
         // was last read right after barrier L-2, which every warp has left
         st_rlx32(&d.run->work[(L + 1) & 1], 0u);
         st_rlx32(&d.run->hub_count[(L + 1) & 1], 0u);
+        st_rlx32(&d.run->hub_cursor[(L + 1) & 1], 0u);
         st_rlx64(&d.run->acc[1 + (L + 1) % 3], 0ull);
       }
       uint32_t found = 0;
@@ -382,8 +413,12 @@ int agile_embedding_bag(agile_ctx *c, uint64_t table_byte0, uint32_t rows, uint3
   if (((uintptr_t)d_out) & 15) return AGILE_EINVAL;
   // rows must not straddle pages: dim*4 divides the page
   if (kPage % (dim * 4)) return AGILE_EINVAL;
-  EmbApp app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, mode};
-  return launch_engine(c, app, stream, warps_for_cache(c, mode == AGILE_ASYNC ? 48 : 4, 32));
+  // one warp per bag while the rows each warp holds or requests ahead fit in the cache
+  uint32_t warps = std::min<uint32_t>(n_bags, warps_for_cache(c, 4, 32));
+  uint64_t ahead = mode == AGILE_ASYNC ? c->dev.nlines / (2ull * warps) : 0;
+  ahead = std::max<uint64_t>(1, std::min<uint64_t>(32, ahead * c->cfg.prefetch_depth));
+  EmbApp app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, mode, (uint32_t)ahead};
+  return launch_engine(c, app, stream, warps);
 }
 
 int agile_bfs(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_t n_vertices, int32_t src,

@@ -70,7 +70,8 @@ struct RunState {
   uint32_t work[4];       // dynamic work counters
   unsigned long long acc[4];  // accumulators (edges scanned, discovered vertices, ...)
   uint32_t flag[4];
-  uint32_t hub_count[2];  // BFS: long adjacency lists queued for slicing, per level parity
+  uint32_t hub_count[2];   // BFS: long adjacency lists queued for slicing, per level parity
+  uint32_t hub_cursor[2];  // BFS: first queued list that may still have slices
 };
 
 struct Dev {
@@ -932,26 +933,28 @@ static __device__ void service_loop(const Dev &d, uint32_t n_app, uint64_t deadl
   uint32_t sw = blockIdx.x, nsw = gridDim.x;
   unsigned l = lane_id();
   uint32_t ns = 32;
-  uint32_t start = (uint32_t)(((uint64_t)sw * 32) % d.Q);
-  for (;;) {
+  uint32_t windows = (d.Q + 31) / 32;
+  for (uint32_t iter = 0;; ++iter) {
     bool progress = false;
-    // device engine: look at 32 queues per step, one per lane
-    for (uint32_t base = 0; base < d.Q; base += 32) {
-      uint32_t qi = start + base + l;
-      uint32_t q = qi % d.Q;
+    // device engine: serve one queue per iteration, the first one with work found from
+    // a start that rotates over the queues and differs between engines, so that every
+    // queue is visited often and commands do not wait behind long scans
+    uint32_t r = (uint32_t)(((uint64_t)iter * nsw + sw) % d.Q);
+    for (uint32_t w = 0; w < windows; ++w) {
+      uint32_t off = w * 32 + l;
+      uint32_t q = (r + off) % d.Q;
       bool has = false;
-      if (base + l < d.Q) {
+      if (off < d.Q) {
         uint32_t *es = &d.emu[q * 4];
         uint32_t db = ld_acq32(&d.sq_db[q]);
         uint32_t f = ld_rlx32(&es[0]);
         has = ((db - (f & d.dmask)) & d.dmask) != 0;
       }
       unsigned m = __ballot_sync(kFull, has);
-      while (m) {
-        int j = __ffs(m) - 1;
-        m &= m - 1;
-        uint32_t qj = __shfl_sync(kFull, q, j);
+      if (m) {
+        uint32_t qj = __shfl_sync(kFull, q, __ffs(m) - 1);
         if (emu_serve(d, qj)) progress = true;
+        break;
       }
     }
     // completion side (Alg. 1) for the queues this warp polls
