@@ -53,18 +53,20 @@ def csrc_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current sources."""
+def recorded_traffic(kernel: str, key: str = "dram_bytes_per_launch"):
+    """Bytes per launch from the committed ncu summary (DRAM, or host link with
+    key="link_bytes_per_launch"), if it was taken on the current sources; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
     cur = csrc_hash()
     for line in open(path):
+        if line.startswith("#"):
+            continue
         parts = dict(p.split("=", 1) for p in line.split() if "=" in p)
         if parts.get("kernel") == kernel and parts.get("source") == cur:
             try:
-                return float(parts["dram_bytes_per_launch"])
+                return float(parts[key])
             except (KeyError, ValueError):
                 return None
     return None
@@ -329,6 +331,7 @@ def run_bfs(args, torch, ag, dev, rank, world):
         "async_over_sync": ms_sync / ms_async,
         "roofline": {"bound": "host_link", "achieved": achieved, "peak": link_peak, "unit": "GB/s",
                      "frac": achieved / link_peak, "traffic": recorded_traffic("engine_kernel<BfsApp>"),
+                     "link_traffic": recorded_traffic("engine_kernel<BfsApp>", "link_bytes_per_launch"),
                      "kernel": "engine_kernel<BfsApp>",
                      "algorithmic_bytes_per_launch": algo_bytes,
                      "peak_source": "measured in this run: pinned host->HBM copy of 1 GiB (copy engine)",
