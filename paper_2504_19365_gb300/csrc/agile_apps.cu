@@ -3,6 +3,9 @@
 // (Sec. 4.5), each in a synchronous and an asynchronous mode.
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <cstdio>
+
 #include "agile.h"
 #include "agile_ctx.cuh"
 #include "agile_dev.cuh"
@@ -151,9 +154,14 @@ struct EmbApp {
 // it go before it requests or waits for any other page.
 struct HubEntry {
   long long s, e;
-  unsigned int next;   // next slice to hand out
-  unsigned int ready;  // level + 1 once s and e are written
+  unsigned int next;  // next slice to hand out
+  unsigned int pad;
+  unsigned long long ready;  // (call epoch << 32) | (level + 1), written after s, e, next
 };
+
+// Every BFS call gets a fresh epoch, so an entry left by an earlier call or level can
+// never look published to a helper that reads it before its new owner has written it.
+static std::atomic<uint64_t> g_bfs_epoch{1};
 
 struct BfsApp {
   uint64_t off_page0, col_page0;
@@ -163,8 +171,11 @@ struct BfsApp {
   uint32_t mode;
   HubEntry *hubq;
   uint32_t hub_cap;
+  uint64_t epoch;
 
   static constexpr uint32_t kChunk = 128;
+
+  __device__ __forceinline__ uint64_t tag(int32_t L) const { return (epoch << 32) | (uint32_t)(L + 1); }
   static constexpr uint32_t kHub = 1024;
   static constexpr uint32_t kSlice = 2048;
 
@@ -245,7 +256,7 @@ struct BfsApp {
           h->e = e;
           h->next = 0;
           __threadfence();
-          st_rel32(&h->ready, (uint32_t)L + 1);
+          st_rel64(&h->ready, tag(L));
         } else {
           hub = false;  // queue full: scanned here
         }
@@ -304,7 +315,8 @@ struct BfsApp {
     unsigned l = lane_id();
     uint32_t ns = 64;
     for (;;) {
-      uint32_t c = 0, i = 0, rd = 0, k = 0;
+      uint32_t c = 0, i = 0, k = 0;
+      uint64_t rd = 0;
       int64_t s = 0, e = 0;
       int act = 0;  // 0 done, 1 slice claimed, 2 retry
       if (l == 0) {
@@ -312,8 +324,8 @@ struct BfsApp {
         i = ld_acq32(&d.run->hub_cursor[L & 1]);
         if (i < c) {
           HubEntry *h = &hubq[i];
-          rd = ld_acq32(&h->ready);
-          if (rd != (uint32_t)L + 1) {
+          rd = ld_acq64(&h->ready);
+          if (rd != tag(L)) {
             act = 2;  // queued, not yet published
           } else {
             s = ld_cg_s64(&h->s);
@@ -398,6 +410,29 @@ __global__ void bfs_init_kernel(int32_t *level, uint32_t n, int32_t src) {
   if (i < n) level[i] = (i == (uint64_t)src) ? 0 : -1;
 }
 
+int bfs_check(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_t n_vertices, int32_t src,
+              int32_t *d_level, uint32_t mode) {
+  if (!c || mode > 1 || !d_level) return AGILE_EINVAL;
+  if (offsets_byte0 % kPage || cols_byte0 % kPage) return AGILE_EINVAL;
+  if (n_vertices == 0 || src < 0 || (uint32_t)src >= n_vertices) return AGILE_EINVAL;
+  if (offsets_byte0 + ((uint64_t)n_vertices + 1) * 8 > c->cfg.store_bytes) return AGILE_EINVAL;
+  if (cols_byte0 >= c->cfg.store_bytes) return AGILE_EINVAL;
+  return AGILE_OK;
+}
+
+int bfs_launch(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_t n_vertices, int32_t src,
+               int32_t *d_level, uint64_t *d_edges_scanned, uint32_t mode, void *stream, HubEntry *hubq,
+               uint32_t hub_cap) {
+  cudaStream_t s = as_stream(stream);
+  bfs_init_kernel<<<(n_vertices + 255) / 256, 256, 0, s>>>(d_level, n_vertices, src);
+  AGILE_CUDA_TRY(cudaGetLastError());
+  if (d_edges_scanned) AGILE_CUDA_TRY(cudaMemsetAsync(d_edges_scanned, 0, 8, s));
+  BfsApp app{offsets_byte0 / kPage, cols_byte0 / kPage, n_vertices, d_level,
+             (unsigned long long *)d_edges_scanned, mode, hubq, hub_cap,
+             g_bfs_epoch.fetch_add(1) & 0xFFFFFFFFull};
+  return launch_engine(c, app, stream, warps_for_cache(c, 4, 32));
+}
+
 }  // namespace
 
 extern "C" {
@@ -423,16 +458,9 @@ int agile_embedding_bag(agile_ctx *c, uint64_t table_byte0, uint32_t rows, uint3
 
 int agile_bfs(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_t n_vertices, int32_t src,
               int32_t *d_level, uint64_t *d_edges_scanned, uint32_t mode, void *stream) {
-  if (!c || mode > 1 || !d_level) return AGILE_EINVAL;
-  if (offsets_byte0 % kPage || cols_byte0 % kPage) return AGILE_EINVAL;
-  if (n_vertices == 0 || src < 0 || (uint32_t)src >= n_vertices) return AGILE_EINVAL;
-  if (offsets_byte0 + ((uint64_t)n_vertices + 1) * 8 > c->cfg.store_bytes) return AGILE_EINVAL;
-  if (cols_byte0 >= c->cfg.store_bytes) return AGILE_EINVAL;
+  int r = bfs_check(c, offsets_byte0, cols_byte0, n_vertices, src, d_level, mode);
+  if (r) return r;
   AGILE_CUDA_TRY(cudaSetDevice(c->device));
-  cudaStream_t s = as_stream(stream);
-  bfs_init_kernel<<<(n_vertices + 255) / 256, 256, 0, s>>>(d_level, n_vertices, src);
-  AGILE_CUDA_TRY(cudaGetLastError());
-  if (d_edges_scanned) AGILE_CUDA_TRY(cudaMemsetAsync(d_edges_scanned, 0, 8, s));
   // queue of long lists: at most (column entries) / kHub of them per level
   uint64_t cap = (c->cfg.store_bytes - cols_byte0) / 4 / BfsApp::kHub + 1;
   if (cap > (1u << 22)) cap = 1u << 22;
@@ -443,9 +471,8 @@ int agile_bfs(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_
     AGILE_CUDA_TRY(cudaMalloc(&c->bfs_hubq, cap * sizeof(HubEntry)));
     c->bfs_hub_cap = (uint32_t)cap;
   }
-  BfsApp app{offsets_byte0 / kPage, cols_byte0 / kPage, n_vertices, d_level,
-             (unsigned long long *)d_edges_scanned, mode, (HubEntry *)c->bfs_hubq, c->bfs_hub_cap};
-  return launch_engine(c, app, stream, warps_for_cache(c, 4, 32));
+  return bfs_launch(c, offsets_byte0, cols_byte0, n_vertices, src, d_level, d_edges_scanned, mode, stream,
+                    (HubEntry *)c->bfs_hubq, c->bfs_hub_cap);
 }
 
 }  // extern "C"
