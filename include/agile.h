@@ -188,6 +188,21 @@ AGILE_API int agile_bfs(agile_ctx *ctx, uint64_t offsets_byte0, uint64_t cols_by
               uint32_t n_vertices, int32_t src, int32_t *d_level,
               uint64_t *d_edges_scanned, uint32_t mode, void *stream);
 
+/* BFS exactly as agile_bfs, for callers that cannot allocate device memory during the
+ * call (code being captured into a CUDA graph, latency-critical loops where an
+ * allocation's device synchronisation is not acceptable).  The paper has no
+ * counterpart: it is an addition of this library.  agile_bfs allocates a queue of long
+ * adjacency lists on first use; this entry point uses a fixed 1 MiB device array
+ * compiled into the library instead and calls no cudaMalloc/cudaFree.
+ * n_cols: number of int32 column entries of the graph; graphs with more than
+ * 33,553,408 column entries (32,768 queue slots of 1,024 entries) are rejected with
+ * AGILE_EINVAL and a message on stderr.  The first call on a device looks up the
+ * array's device address (make that first call before any stream capture).  All calls
+ * on a device share the array: calls of this entry point that overlap on one GPU race. */
+AGILE_API int agile_bfs_noalloc(agile_ctx *ctx, uint64_t offsets_byte0, uint64_t cols_byte0,
+                                uint32_t n_vertices, uint64_t n_cols, int32_t src, int32_t *d_level,
+                                uint64_t *d_edges_scanned, uint32_t mode, void *stream);
+
 /* Validation entry point: serve store pages d_pages[0..n) one at a time, in order, by
  * a single GPU thread (sync mode), and write the outcome of each request to
  * d_codes[i] (0 hit, 1 fill of an INVALID way, 2 eviction of a READY line, 3

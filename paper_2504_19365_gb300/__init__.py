@@ -35,6 +35,7 @@ EXPORTED = [
     "agile_config_default", "agile_init", "agile_destroy", "agile_store_write",
     "agile_store_read", "agile_read_async", "agile_write_async", "agile_wait",
     "agile_prefetch", "agile_flush", "agile_invalidate", "agile_embedding_bag", "agile_bfs",
+    "agile_bfs_noalloc",
     "agile_cache_replay", "agile_cache_tags", "agile_cache_lines", "agile_cache_sets",
     "agile_stats", "agile_reset_stats", "agile_check", "agile_launch_shape", "agile_strerror",
 ]
@@ -106,6 +107,7 @@ def lib():
             "agile_invalidate": (C.c_int, [vp, vp]),
             "agile_embedding_bag": (C.c_int, [vp, u64, u32, u32, vp, vp, u32, vp, u32, vp]),
             "agile_bfs": (C.c_int, [vp, u64, u64, u32, i32, vp, vp, u32, vp]),
+            "agile_bfs_noalloc": (C.c_int, [vp, u64, u64, u32, u64, i32, vp, vp, u32, vp]),
             "agile_cache_replay": (C.c_int, [vp, vp, u32, vp, vp]),
             "agile_cache_tags": (C.c_int, [vp, vp]),
             "agile_cache_lines": (u64, [vp]),
@@ -197,6 +199,13 @@ def agile_embedding_bag(ctx, table_byte0, rows, dim, d_idx, d_offsets, n_bags, d
 def agile_bfs(ctx, offsets_byte0, cols_byte0, n_vertices, src, d_level, d_edges, mode, stream) -> int:
     return _ok(lib().agile_bfs(ctx, offsets_byte0, cols_byte0, n_vertices, src, d_level, d_edges, mode,
                                stream), "agile_bfs")
+
+
+def agile_bfs_noalloc(ctx, offsets_byte0, cols_byte0, n_vertices, n_cols, src, d_level, d_edges, mode,
+                      stream) -> int:
+    """BFS that allocates nothing during the call (scratch in a fixed device array)."""
+    return _ok(lib().agile_bfs_noalloc(ctx, offsets_byte0, cols_byte0, n_vertices, n_cols, src, d_level,
+                                       d_edges, mode, stream), "agile_bfs_noalloc")
 
 
 def agile_cache_replay(ctx, d_pages, n, d_codes, stream) -> int:

@@ -5,6 +5,7 @@
 
 #include <atomic>
 #include <cstdio>
+#include <mutex>
 
 #include "agile.h"
 #include "agile_ctx.cuh"
@@ -433,6 +434,41 @@ int bfs_launch(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32
   return launch_engine(c, app, stream, warps_for_cache(c, 4, 32));
 }
 
+// ---------------------------------------------------------------- BFS without allocation
+// Some callers cannot call cudaMalloc when they run a BFS: code recorded into a CUDA
+// graph or running under stream capture (allocation is not allowed there), and
+// latency-critical loops in which an allocation's implicit device synchronisation
+// would stall every other stream.  For them agile_bfs_noalloc keeps the long-list
+// queue, the only scratch the BFS kernel needs beyond the context, in this fixed
+// device array.  Every GPU that loads the library holds it (1 MiB) until the process
+// exits.  Host code must not pass the array's name to a kernel: on the host it is a
+// stand-in symbol, not a device address, so its address is fetched once per device with
+// cudaGetSymbolAddress, with that device current, on the first call on that device.
+// No field needs clearing between calls: an entry is written before it is published,
+// and publication carries the call's epoch, so what an earlier call left behind is never
+// taken for a live entry.  All calls on one device share the array, so calls of this
+// entry point that overlap on that GPU (from any context or stream) race on it.
+constexpr uint32_t kNoAllocHubMax = 32768;
+static __device__ __align__(256) HubEntry g_bfs_hub_scratch[kNoAllocHubMax];
+
+int noalloc_scratch(int device, HubEntry **out) {
+  static std::mutex mu;
+  static HubEntry *ptr[128] = {};
+  if (device < 0 || device >= 128) return AGILE_ENODEV;
+  std::lock_guard<std::mutex> g(mu);
+  if (!ptr[device]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_bfs_hub_scratch);
+    if (e != cudaSuccess || !p) {
+      fprintf(stderr, "agile: cudaGetSymbolAddress of the BFS scratch failed: %s\n", cudaGetErrorString(e));
+      return AGILE_ECUDA;
+    }
+    ptr[device] = (HubEntry *)p;
+  }
+  *out = ptr[device];
+  return AGILE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -473,6 +509,28 @@ int agile_bfs(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_
   }
   return bfs_launch(c, offsets_byte0, cols_byte0, n_vertices, src, d_level, d_edges_scanned, mode, stream,
                     (HubEntry *)c->bfs_hubq, c->bfs_hub_cap);
+}
+
+int agile_bfs_noalloc(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_t n_vertices,
+                      uint64_t n_cols, int32_t src, int32_t *d_level, uint64_t *d_edges_scanned, uint32_t mode,
+                      void *stream) {
+  int r = bfs_check(c, offsets_byte0, cols_byte0, n_vertices, src, d_level, mode);
+  if (r) return r;
+  if (n_cols > (c->cfg.store_bytes - cols_byte0) / 4) return AGILE_EINVAL;
+  if (n_cols / BfsApp::kHub + 1 > kNoAllocHubMax) {
+    fprintf(stderr,
+            "agile_bfs_noalloc: %llu column entries need up to %llu long-list slots; this entry point "
+            "has %u (graphs up to %llu column entries); use agile_bfs\n",
+            (unsigned long long)n_cols, (unsigned long long)(n_cols / BfsApp::kHub + 1), kNoAllocHubMax,
+            (unsigned long long)(kNoAllocHubMax - 1) * BfsApp::kHub);
+    return AGILE_EINVAL;
+  }
+  AGILE_CUDA_TRY(cudaSetDevice(c->device));
+  HubEntry *scratch = nullptr;
+  r = noalloc_scratch(c->device, &scratch);
+  if (r) return r;
+  return bfs_launch(c, offsets_byte0, cols_byte0, n_vertices, src, d_level, d_edges_scanned, mode, stream,
+                    scratch, kNoAllocHubMax);
 }
 
 }  // extern "C"
