@@ -308,54 +308,66 @@ struct BfsApp {
     return true;
   }
 
-  // Take slices of the queued long lists of level L until none is left.  All warps work
-  // on the first list that still has slices (a shared cursor moves past exhausted
-  // lists), so a helper never walks the whole queue.  Lists queued after this warp
-  // leaves are sliced by the warps that queued them, which run this same loop.
+  // Take slices of the queued long lists of level L until none is left.  A warp looks
+  // at 32 queued lists at once (one per lane, from a shared cursor), claims a slice of
+  // one that still has slices (different warps pick different lists), and moves the
+  // cursor past the leading lists that are used up, so the cost per warp grows with
+  // the number of lists / 32, not with the number of lists.  Lists queued after this
+  // warp leaves are sliced by the warps that queued them, which run this same loop.
   __device__ bool help_hubs(const Dev &d, const AppCtx &a, int32_t L, uint32_t &found, Pin &pc) const {
     unsigned l = lane_id();
     uint32_t ns = 64;
+    const uint64_t want_tag = tag(L);
     for (;;) {
-      uint32_t c = 0, i = 0, k = 0;
-      uint64_t rd = 0;
-      int64_t s = 0, e = 0;
-      int act = 0;  // 0 done, 1 slice claimed, 2 retry
+      uint32_t c = 0, cur = 0;
       if (l == 0) {
         c = min(ld_acq32(&d.run->hub_count[L & 1]), hub_cap);
-        i = ld_acq32(&d.run->hub_cursor[L & 1]);
-        if (i < c) {
-          HubEntry *h = &hubq[i];
-          rd = ld_acq64(&h->ready);
-          if (rd != tag(L)) {
-            act = 2;  // queued, not yet published
-          } else {
-            s = ld_cg_s64(&h->s);
-            e = ld_cg_s64(&h->e);
-            uint32_t slices = (uint32_t)((e - s + kSlice - 1) / kSlice);
-            k = atomicAdd(&h->next, 1u);
-            if (k < slices) {
-              act = 1;
-            } else {
-              atomicCAS(&d.run->hub_cursor[L & 1], i, i + 1);
-              act = 3;  // exhausted: look again at once
-            }
-          }
+        cur = ld_acq32(&d.run->hub_cursor[L & 1]);
+      }
+      c = __shfl_sync(kFull, c, 0);
+      cur = __shfl_sync(kFull, cur, 0);
+      if (cur >= c) return true;
+      uint32_t i = cur + l;
+      bool in = i < c, ready = false, left = false;
+      int64_t s = 0, e = 0;
+      uint32_t slices = 0;
+      if (in) {
+        HubEntry *h = &hubq[i];
+        ready = ld_acq64(&h->ready) == want_tag;
+        if (ready) {
+          s = ld_cg_s64(&h->s);
+          e = ld_cg_s64(&h->e);
+          slices = (uint32_t)((e - s + kSlice - 1) / kSlice);
+          left = ld_rlx32(&h->next) < slices;
         }
       }
-      act = __shfl_sync(kFull, act, 0);
-      if (act == 0) return true;
-      if (act == 3) continue;
-      if (act == 2) {
+      unsigned m = __ballot_sync(kFull, left);
+      unsigned used = __ballot_sync(kFull, !in || (ready && !left));
+      // leading lists that are used up: move the shared cursor past them
+      uint32_t lead = (used == kFull) ? 32u : (uint32_t)(__ffs(~used) - 1);
+      if (lead && l == 0) atomicMax(&d.run->hub_cursor[L & 1], min(cur + lead, c));
+      if (!m) {
+        if (lead) continue;
         if (gtimer() > a.deadline || aborted(d)) {
           if (l == 0) set_error(d, -110);
           return false;
         }
-        backoff(ns);
+        backoff(ns);  // queued lists not yet published
         continue;
       }
-      s = __shfl_sync(kFull, s, 0);
-      e = __shfl_sync(kFull, e, 0);
-      k = __shfl_sync(kFull, k, 0);
+      // pick one of the lists with slices left; spread warps over them
+      uint32_t nth = a.warp % __popc(m);
+      unsigned mm = m;
+      for (uint32_t t = 0; t < nth; ++t) mm &= mm - 1;
+      int j = __ffs(mm) - 1;
+      uint32_t k = 0;
+      if (l == (unsigned)j) k = atomicAdd(&hubq[i].next, 1u);
+      k = __shfl_sync(kFull, k, j);
+      s = __shfl_sync(kFull, s, j);
+      e = __shfl_sync(kFull, e, j);
+      slices = __shfl_sync(kFull, slices, j);
+      if (k >= slices) continue;  // lost the race for its last slice
+      ns = 64;
       int64_t p0 = s + (int64_t)k * kSlice, p1 = min(e, p0 + (int64_t)kSlice);
       for (int64_t pos = p0 + l; pos - l < p1; pos += 32) {
         bool on = pos < p1;
