@@ -149,8 +149,10 @@ struct EmbApp {
 // the grid barrier that ends the level; the search stops when a level discovers
 // nothing.  Edges scanned = sum of the degrees of the frontier vertices of all levels.
 //   SYNC : each page (offsets, columns) is requested when needed and waited for.
-//   ASYNC: the offsets pages of a sub-chunk and the first 32 pages of its column span
-//          are issued before any of them is read.
+//   ASYNC: a three-stage software pipeline over 32-vertex units: while the warp scans
+//          unit i, the offsets of unit i+1 are read and the pages of its lists are
+//          issued, and the offsets pages of unit i+2 are issued; a long-list slice
+//          issues all of its pages before it is scanned.
 // A warp keeps at most one line pinned between steps (the page it read last) and lets
 // it go before it requests or waits for any other page.
 struct HubEntry {
@@ -228,42 +230,29 @@ struct BfsApp {
     }
   }
 
-  __device__ bool chunk(const Dev &d, const AppCtx &a, uint32_t v0, int32_t L, uint32_t &found,
-                        unsigned long long &scanned, Pin &pc) const {
-    unsigned l = lane_id();
-    uint32_t v = v0 + l;
-    bool f = v < n && ld_rlx32((const uint32_t *)&level[v]) == (uint32_t)L;
-    if (!__any_sync(kFull, f)) return true;
-    const bool async = mode == AGILE_ASYNC;
-    if (async) {
-      uint64_t pa = off_page0 + ((uint64_t)v * 8) / kPage, pb = off_page0 + ((uint64_t)v * 8 + 8) / kPage;
-      bool need_a = f && !(pc.valid && pc.page == pa), need_b = f && pb != pa && !(pc.valid && pc.page == pb);
-      if (__any_sync(kFull, need_a) && !warp_request(d, need_a, pa, a.q0, false, a.deadline)) return false;
-      if (__any_sync(kFull, need_b) && !warp_request(d, need_b, pb, a.q0, false, a.deadline)) return false;
-    }
-    int64_t s = 0, e = 0;
-    if (!gather<int64_t>(d, a, off_page0, f, (uint64_t)v * 8, s, pc)) return false;
-    if (!gather<int64_t>(d, a, off_page0, f, (uint64_t)v * 8 + 8, e, pc)) return false;
-    uint32_t deg = f ? (uint32_t)(e - s) : 0;
-    scanned += __reduce_add_sync(kFull, deg);
-    // long lists go to the slice queue
+  // queue a list of at least kHub entries for slicing; false if this lane keeps it
+  __device__ bool push_hub(const Dev &d, uint32_t deg, int64_t s, int64_t e, int32_t L) const {
     bool hub = deg >= kHub;
-    if (__any_sync(kFull, hub)) {
-      if (hub) {
-        uint32_t idx = atomicAdd(&d.run->hub_count[L & 1], 1u);
-        if (idx < hub_cap) {
-          HubEntry *h = &hubq[idx];
-          h->s = s;
-          h->e = e;
-          h->next = 0;
-          __threadfence();
-          st_rel64(&h->ready, tag(L));
-        } else {
-          hub = false;  // queue full: scanned here
-        }
+    if (__any_sync(kFull, hub) && hub) {
+      uint32_t idx = atomicAdd(&d.run->hub_count[L & 1], 1u);
+      if (idx < hub_cap) {
+        HubEntry *h = &hubq[idx];
+        h->s = s;
+        h->e = e;
+        h->next = 0;
+        __threadfence();
+        st_rel64(&h->ready, tag(L));
+      } else {
+        hub = false;  // queue full: scanned here
       }
     }
-    uint32_t dg = hub ? 0 : deg;
+    return hub;
+  }
+
+  // scan the lists [s, s + dg) of the lanes, flattened over the warp (32 entries a step)
+  __device__ bool scan_lists(const Dev &d, const AppCtx &a, int64_t s, uint32_t dg, int32_t L, uint32_t &found,
+                             Pin &pc) const {
+    unsigned l = lane_id();
     uint32_t incl = dg;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -272,21 +261,6 @@ struct BfsApp {
     }
     uint32_t excl = incl - dg;
     uint32_t total = __shfl_sync(kFull, incl, 31);
-    if (total == 0) return true;
-    if (async) {
-      // the lists of 32 consecutive vertices lie in one contiguous span of the column
-      // array: issue its first 32 pages at once
-      int64_t lo = dg ? s : INT64_MAX, hi = dg ? e - 1 : -1;
-#pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) {
-        lo = min(lo, (int64_t)__shfl_xor_sync(kFull, lo, o));
-        hi = max(hi, (int64_t)__shfl_xor_sync(kFull, hi, o));
-      }
-      uint64_t p0 = col_page0 + ((uint64_t)lo * 4) / kPage, p1 = col_page0 + ((uint64_t)hi * 4) / kPage;
-      uint64_t pg = p0 + l;
-      bool want = pg <= p1 && !(pc.valid && pc.page == pg);
-      if (__any_sync(kFull, want) && !warp_request(d, want, pg, a.q0, false, a.deadline)) return false;
-    }
     for (uint32_t k0 = 0; k0 < total; k0 += 32) {
       uint32_t k = k0 + l;
       bool act = k < total;
@@ -306,6 +280,105 @@ struct BfsApp {
       visit(act, u, L, found);
     }
     return true;
+  }
+
+  // synchronous processing of one 32-vertex unit: every page when needed
+  __device__ bool chunk(const Dev &d, const AppCtx &a, uint32_t v0, int32_t L, uint32_t &found,
+                        unsigned long long &scanned, Pin &pc) const {
+    uint32_t v = v0 + lane_id();
+    bool f = v < n && ld_rlx32((const uint32_t *)&level[v]) == (uint32_t)L;
+    if (!__any_sync(kFull, f)) return true;
+    int64_t s = 0, e = 0;
+    if (!gather<int64_t>(d, a, off_page0, f, (uint64_t)v * 8, s, pc)) return false;
+    if (!gather<int64_t>(d, a, off_page0, f, (uint64_t)v * 8 + 8, e, pc)) return false;
+    uint32_t deg = f ? (uint32_t)(e - s) : 0;
+    scanned += __reduce_add_sync(kFull, deg);
+    bool hub = push_hub(d, deg, s, e, L);
+    return scan_lists(d, a, s, hub ? 0 : deg, L, found, pc);
+  }
+
+  // ---- asynchronous pipeline over 32-vertex units (ASYNC mode) ---------------------
+  // Next unit of this warp with at least one frontier vertex; chunks of kChunk ids are
+  // claimed from the level's counter as needed.
+  __device__ bool next_unit(const Dev &d, int32_t L, uint32_t nchunks, uint32_t &chunk, uint32_t &sub,
+                            uint32_t &v0, bool &f) const {
+    for (;;) {
+      if (sub >= kChunk) {
+        uint32_t c = 0;
+        if (lane_id() == 0) c = atomicAdd(&d.run->work[L & 1], 1u);
+        chunk = __shfl_sync(kFull, c, 0);
+        sub = 0;
+        if (chunk >= nchunks || aborted(d)) return false;
+      }
+      v0 = chunk * kChunk + sub;
+      sub += 32;
+      uint32_t v = v0 + lane_id();
+      f = v < n && ld_rlx32((const uint32_t *)&level[v]) == (uint32_t)L;
+      if (__any_sync(kFull, f)) return true;
+    }
+  }
+
+  // stage A: issue the offsets pages of a unit
+  __device__ bool stage_a(const Dev &d, const AppCtx &a, uint32_t v0, bool f, const Pin &pc) const {
+    uint32_t v = v0 + lane_id();
+    uint64_t pa = off_page0 + ((uint64_t)v * 8) / kPage, pb = off_page0 + ((uint64_t)v * 8 + 8) / kPage;
+    bool need_a = f && !(pc.valid && pc.page == pa), need_b = f && pb != pa && !(pc.valid && pc.page == pb);
+    if (__any_sync(kFull, need_a) && !warp_request(d, need_a, pa, a.q0, false, a.deadline)) return false;
+    if (__any_sync(kFull, need_b) && !warp_request(d, need_b, pb, a.q0, false, a.deadline)) return false;
+    return true;
+  }
+
+  // stage B: read the offsets, queue long lists, issue the unit's column span; returns the
+  // start and the degree left to scan here (0 for queued long lists)
+  __device__ bool stage_b(const Dev &d, const AppCtx &a, uint32_t v0, bool f, int32_t L, int64_t &s, uint32_t &dg,
+                          unsigned long long &scanned, Pin &pc) const {
+    uint32_t v = v0 + lane_id();
+    int64_t e = 0;
+    s = 0;
+    if (!gather<int64_t>(d, a, off_page0, f, (uint64_t)v * 8, s, pc)) return false;
+    if (!gather<int64_t>(d, a, off_page0, f, (uint64_t)v * 8 + 8, e, pc)) return false;
+    uint32_t deg = f ? (uint32_t)(e - s) : 0;
+    scanned += __reduce_add_sync(kFull, deg);
+    bool hub = push_hub(d, deg, s, e, L);
+    dg = hub ? 0 : deg;
+    // a list shorter than kHub entries spans at most two pages: issue exactly those
+    uint64_t pa = col_page0 + ((uint64_t)s * 4) / kPage;
+    uint64_t pb = col_page0 + ((uint64_t)(dg ? e - 1 : s) * 4) / kPage;
+    bool want_a = dg && !(pc.valid && pc.page == pa);
+    bool want_b = dg && pb != pa && !(pc.valid && pc.page == pb);
+    if (__any_sync(kFull, want_a) && !warp_request(d, want_a, pa, a.q0, false, a.deadline)) return false;
+    if (__any_sync(kFull, want_b) && !warp_request(d, want_b, pb, a.q0, false, a.deadline)) return false;
+    return true;
+  }
+
+  // stage C: scan the unit's lists (flattened over the warp)
+  __device__ bool stage_c(const Dev &d, const AppCtx &a, int64_t s, uint32_t dg, int32_t L, uint32_t &found,
+                          Pin &pc) const {
+    return scan_lists(d, a, s, dg, L, found, pc);
+  }
+
+  __device__ bool run_async_units(const Dev &d, const AppCtx &a, int32_t L, uint32_t nchunks, uint32_t &found,
+                                  unsigned long long &scanned, Pin &pc) const {
+    uint32_t chunk = 0, sub = kChunk;
+    uint32_t v1 = 0, v2 = 0;
+    bool f1 = false, f2 = false;
+    int64_t s0 = 0, s1 = 0;
+    uint32_t dg0 = 0, dg1 = 0;
+    bool have0 = false, have1 = next_unit(d, L, nchunks, chunk, sub, v1, f1), have2 = false;
+    if (have1 && !stage_a(d, a, v1, f1, pc)) return false;
+    for (;;) {
+      have2 = have1 && next_unit(d, L, nchunks, chunk, sub, v2, f2);
+      if (have2 && !stage_a(d, a, v2, f2, pc)) return false;
+      if (have1 && !stage_b(d, a, v1, f1, L, s1, dg1, scanned, pc)) return false;
+      if (have0 && !stage_c(d, a, s0, dg0, L, found, pc)) return false;
+      have0 = have1;
+      s0 = s1;
+      dg0 = dg1;
+      have1 = have2;
+      v1 = v2;
+      f1 = f2;
+      if (!have0 && !have1) return true;
+    }
   }
 
   // Take slices of the queued long lists of level L until none is left.  A warp looks
@@ -369,6 +442,12 @@ struct BfsApp {
       if (k >= slices) continue;  // lost the race for its last slice
       ns = 64;
       int64_t p0 = s + (int64_t)k * kSlice, p1 = min(e, p0 + (int64_t)kSlice);
+      if (mode == AGILE_ASYNC) {
+        uint64_t q0p = col_page0 + ((uint64_t)p0 * 4) / kPage, q1p = col_page0 + ((uint64_t)(p1 - 1) * 4) / kPage;
+        uint64_t pg = q0p + l;
+        bool want = pg <= q1p && !(pc.valid && pc.page == pg);
+        if (__any_sync(kFull, want) && !warp_request(d, want, pg, a.q0, false, a.deadline)) return false;
+      }
       for (int64_t pos = p0 + l; pos - l < p1; pos += 32) {
         bool on = pos < p1;
         int32_t u = 0;
@@ -395,13 +474,17 @@ struct BfsApp {
       uint32_t found = 0;
       Pin pc{0, 0, false};
       bool ok = true;
-      for (;;) {
-        uint32_t c = 0;
-        if (l == 0) c = atomicAdd(&d.run->work[L & 1], 1u);
-        c = __shfl_sync(kFull, c, 0);
-        if (c >= nchunks || aborted(d)) break;
-        for (uint32_t sub = 0; sub < kChunk && ok; sub += 32) ok = chunk(d, a, c * kChunk + sub, L, found, scanned, pc);
-        if (!ok) break;
+      if (mode == AGILE_ASYNC) {
+        ok = run_async_units(d, a, L, nchunks, found, scanned, pc);
+      } else {
+        for (;;) {
+          uint32_t c = 0;
+          if (l == 0) c = atomicAdd(&d.run->work[L & 1], 1u);
+          c = __shfl_sync(kFull, c, 0);
+          if (c >= nchunks || aborted(d)) break;
+          for (uint32_t sub = 0; sub < kChunk && ok; sub += 32) ok = chunk(d, a, c * kChunk + sub, L, found, scanned, pc);
+          if (!ok) break;
+        }
       }
       if (ok) help_hubs(d, a, L, found, pc);
       release(d, pc);
@@ -443,7 +526,9 @@ int bfs_launch(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32
   BfsApp app{offsets_byte0 / kPage, cols_byte0 / kPage, n_vertices, d_level,
              (unsigned long long *)d_edges_scanned, mode, hubq, hub_cap,
              g_bfs_epoch.fetch_add(1) & 0xFFFFFFFFull};
-  return launch_engine(c, app, stream, warps_for_cache(c, 4, 32));
+  // sync: about two lines per warp (one pinned, one being filled); async: four, since a
+  // warp also holds the pages it requested for its next units
+  return launch_engine(c, app, stream, warps_for_cache(c, mode == AGILE_ASYNC ? 4 : 2, 32));
 }
 
 // ---------------------------------------------------------------- BFS without allocation
