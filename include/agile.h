@@ -179,6 +179,21 @@ AGILE_API int agile_embedding_bag(agile_ctx *ctx, uint64_t table_byte0, uint32_t
                         const int64_t *d_idx, const int64_t *d_offsets, uint32_t n_bags,
                         float *d_out, uint32_t mode, void *stream);
 
+/* Backward of agile_embedding_bag with a fused SGD step (differentiable extension of
+ * the Sec. 4.4 lookups).  Same table and bag arguments as the forward; n_indices =
+ * d_offsets[n_bags] (the length of d_idx); d_grad_out: n_bags*dim floats.
+ * G[r][d] = sum over positions i with d_idx[i] = r of d_grad_out[bag(i)][d], added in
+ * increasing i in FP32.  If d_grad_table != NULL it receives G (rows*dim floats, rows
+ * never indexed are 0).  If lr != 0 every touched row is updated in the cache as
+ * T[r][d] - (lr * G[r][d]) (product rounded first) and its line becomes MODIFIED; the
+ * store sees the new rows after eviction write-backs or agile_flush.  mode AGILE_ASYNC
+ * requests the pages of upcoming rows ahead.  Uses library scratch (sorted keys). */
+AGILE_API int agile_embedding_bag_backward(agile_ctx *ctx, uint64_t table_byte0, uint32_t rows,
+                                           uint32_t dim, const int64_t *d_idx,
+                                           const int64_t *d_offsets, uint32_t n_bags,
+                                           uint32_t n_indices, const float *d_grad_out, float lr,
+                                           float *d_grad_table, uint32_t mode, void *stream);
+
 /* Breadth-first search over a CSR graph on the store (Sec. 4.5): int64 offsets
  * [n_vertices+1] at byte offsets_byte0, int32 columns at byte cols_byte0 (both
  * multiples of 4096).  d_level[v] = BFS level of v from src, -1 when unreachable.
