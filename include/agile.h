@@ -194,6 +194,21 @@ AGILE_API int agile_embedding_bag_backward(agile_ctx *ctx, uint64_t table_byte0,
                                            uint32_t n_indices, const float *d_grad_out, float lr,
                                            float *d_grad_table, uint32_t mode, void *stream);
 
+/* Lookup + compute pipeline (the overlap experiment: Sec. 4.2 computation-to-
+ * communication ratio, Sec. 4.4 prefetching the next batch while computing).
+ * n_tables FP32 tables of rows x dim, table k at byte table_byte0 + k*table_stride
+ * (both multiples of 4096).  d_idx: int64 [n_batches][n_tables][n_bags][pooling] row
+ * numbers.  For every (batch t, bag b): out[t][b][k*dim + d] = sum over p of
+ * T_k[idx[t][k][b][p]][d] in increasing p (FP32), then compute_iters rounds of
+ * x = fma(x, 1 - 2^-12, 2^-10) per element.  d_out: float [n_batches][n_bags][n_tables*dim].
+ * AGILE_SYNC requests each row when summed; AGILE_ASYNC requests a warp's next unit
+ * of work before gathering and computing the current one. */
+AGILE_API int agile_embedding_pipeline(agile_ctx *ctx, uint64_t table_byte0, uint64_t table_stride,
+                                       uint32_t n_tables, uint32_t rows, uint32_t dim,
+                                       const int64_t *d_idx, uint32_t pooling, uint32_t n_bags,
+                                       uint32_t n_batches, uint32_t compute_iters, float *d_out,
+                                       uint32_t mode, void *stream);
+
 /* Breadth-first search over a CSR graph on the store (Sec. 4.5): int64 offsets
  * [n_vertices+1] at byte offsets_byte0, int32 columns at byte cols_byte0 (both
  * multiples of 4096).  d_level[v] = BFS level of v from src, -1 when unreachable.

@@ -12,6 +12,7 @@ Functions and the passage each restates:
                                        Sec. 4.4
   embedding_bag / _backward / sgd   -- sum-pooled lookups of Sec. 4.4, fixed order
   bfs                               -- FIFO-queue BFS over CSR (Sec. 4.5)
+  fma_chain / embedding_pipeline    -- compute phase of the overlap experiment (Sec. 4.2)
   ideal_speedup                     -- Eq. 1
   set_of                            -- the cache's set-index function
 
@@ -67,6 +68,7 @@ def lib():
         L.orc_sgd.argtypes = [vp, u64, u32, vp, vp, C.c_float]
         L.orc_bfs.argtypes = [u64, vp, vp, i32, vp]
         L.orc_bfs.restype = u64
+        L.orc_fma_chain.argtypes = [vp, u64, u32, C.c_float, C.c_float]
         L.orc_ideal_speedup.argtypes = [C.c_double]
         L.orc_ideal_speedup.restype = C.c_double
         _lib = L
@@ -208,6 +210,34 @@ def bfs(offsets: np.ndarray, cols: np.ndarray, src: int):
     level = np.empty(max(n, 1), dtype=np.int32)
     scanned = int(lib().orc_bfs(n, _p(o), _p(c), int(src), _p(level)))
     return level[:n], scanned
+
+
+FMA_A = 0.999755859375   # 1 - 2^-12
+FMA_B = 0.0009765625     # 2^-10
+
+
+def fma_chain(x: np.ndarray, iters: int, a: float = FMA_A, b: float = FMA_B) -> np.ndarray:
+    """Compute phase of the overlap experiment: `iters` rounds of x = fma(x, a, b)."""
+    y = np.array(x, dtype=np.float32, copy=True, order="C")
+    lib().orc_fma_chain(_p(y), y.size, iters, a, b)
+    return y
+
+
+def embedding_pipeline(tables, idx, pooling: int, iters: int) -> np.ndarray:
+    """Lookup batches over several tables followed by the compute phase.
+
+    tables: list of (rows, dim) float32 arrays; idx: int64 [batches, tables, bags, pooling].
+    Returns float32 [batches, bags, tables * dim]: the sum-pooled rows of every table,
+    concatenated per bag, then `iters` multiply-add rounds per element."""
+    nb_t, nt, nbags, pool = idx.shape
+    assert pool == pooling and nt == len(tables)
+    dim = tables[0].shape[1]
+    out = np.empty((nb_t, nbags, nt * dim), dtype=np.float32)
+    off = np.arange(nbags + 1, dtype=np.int64) * pooling
+    for t in range(nb_t):
+        for k in range(nt):
+            out[t, :, k * dim:(k + 1) * dim] = embedding_bag(tables[k], idx[t, k].reshape(-1), off)
+    return fma_chain(out, iters)
 
 
 def ideal_speedup(ctc: float) -> float:

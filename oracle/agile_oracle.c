@@ -19,10 +19,13 @@
  *                           element, indices added in increasing order (Sec. 4.4 DLRM
  *                           lookups); backward scatter-add and an SGD step.
  *   - BFS                 : textbook FIFO-queue breadth-first search over CSR (Sec. 4.5).
+ *   - compute phase       : the FP32 multiply-add chain that follows each lookup batch
+ *                           in the overlap experiment (Sec. 4.2).
  *   - ideal speedup       : Eq. 1.
  *
  * Floating point: compiled with -ffp-contract=off so that a*b+c is never fused.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -285,6 +288,22 @@ void orc_sgd(float *table, uint64_t rows, uint32_t dim, const float *G, const ui
       float step = lr * G[r * dim + d];
       table[r * dim + d] = table[r * dim + d] - step;
     }
+  }
+}
+
+/* ------------------------------------------------------------------ compute phase */
+
+/*
+ * Synthetic FP32 compute that follows each lookup batch in the overlap experiment
+ * (Sec. 4.2: computation whose length sets the computation-to-communication ratio):
+ * every element goes through `iters` fused multiply-adds x = fma(x, a, b), each
+ * rounded once (C99 fmaf).
+ */
+void orc_fma_chain(float *x, uint64_t n, uint32_t iters, float a, float b) {
+  for (uint64_t i = 0; i < n; ++i) {
+    float v = x[i];
+    for (uint32_t k = 0; k < iters; ++k) v = fmaf(v, a, b);
+    x[i] = v;
   }
 }
 

@@ -35,7 +35,7 @@ EXPORTED = [
     "agile_config_default", "agile_init", "agile_destroy", "agile_store_write",
     "agile_store_read", "agile_read_async", "agile_write_async", "agile_wait",
     "agile_prefetch", "agile_flush", "agile_invalidate", "agile_embedding_bag",
-    "agile_embedding_bag_backward", "agile_bfs",
+    "agile_embedding_bag_backward", "agile_embedding_pipeline", "agile_bfs",
     "agile_bfs_noalloc",
     "agile_cache_replay", "agile_cache_tags", "agile_cache_lines", "agile_cache_sets",
     "agile_stats", "agile_reset_stats", "agile_check", "agile_launch_shape", "agile_strerror",
@@ -109,6 +109,8 @@ def lib():
             "agile_embedding_bag": (C.c_int, [vp, u64, u32, u32, vp, vp, u32, vp, u32, vp]),
             "agile_embedding_bag_backward": (C.c_int, [vp, u64, u32, u32, vp, vp, u32, u32, vp, C.c_float, vp,
                                                        u32, vp]),
+            "agile_embedding_pipeline": (C.c_int, [vp, u64, u64, u32, u32, u32, vp, u32, u32, u32, u32, vp, u32,
+                                                   vp]),
             "agile_bfs": (C.c_int, [vp, u64, u64, u32, i32, vp, vp, u32, vp]),
             "agile_bfs_noalloc": (C.c_int, [vp, u64, u64, u32, u64, i32, vp, vp, u32, vp]),
             "agile_cache_replay": (C.c_int, [vp, vp, u32, vp, vp]),
@@ -204,6 +206,13 @@ def agile_embedding_bag_backward(ctx, table_byte0, rows, dim, d_idx, d_offsets, 
     return _ok(lib().agile_embedding_bag_backward(ctx, table_byte0, rows, dim, d_idx, d_offsets, n_bags, n_indices,
                                                   d_grad_out, lr, d_grad_table, mode, stream),
                "agile_embedding_bag_backward")
+
+
+def agile_embedding_pipeline(ctx, table_byte0, table_stride, n_tables, rows, dim, d_idx, pooling, n_bags, n_batches,
+                             compute_iters, d_out, mode, stream) -> int:
+    return _ok(lib().agile_embedding_pipeline(ctx, table_byte0, table_stride, n_tables, rows, dim, d_idx, pooling,
+                                              n_bags, n_batches, compute_iters, d_out, mode, stream),
+               "agile_embedding_pipeline")
 
 
 def agile_bfs(ctx, offsets_byte0, cols_byte0, n_vertices, src, d_level, d_edges, mode, stream) -> int:

@@ -31,6 +31,7 @@ constexpr int kMaxF4 = 8;  // float4 columns per lane: dim <= 32 * 4 * 8 = 1024
 //          (Sec. 4.4 "AGILE async": prefetch ahead of the computation).  `ahead` is
 //          sized from the cache so that rows requested ahead are not evicted before
 //          they are used.
+template <int MF4>
 struct EmbApp {
   uint64_t page0;  // first store page of the table
   uint32_t rows, dim;
@@ -91,9 +92,9 @@ struct EmbApp {
     if (async && !issue_rows(d, a, pf, ahead)) return;
     for (uint32_t b = a.warp; b < n_bags; b += a.n_warps) {
       int64_t s = off[b], e = off[b + 1];
-      float4 acc[kMaxF4];
+      float4 acc[MF4];
 #pragma unroll
-      for (int k = 0; k < kMaxF4; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int k = 0; k < MF4; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
       for (int64_t i0 = s; i0 < e; i0 += 32) {
         int64_t i = i0 + l;
         uint64_t r = i < e ? (uint64_t)idx[i] : 0;
@@ -112,7 +113,7 @@ struct EmbApp {
           if (!warp_pin_page(d, pg, a.q0, a.deadline, line)) return;
           const uint8_t *rowp = line_ptr(d, line) + inpage;
 #pragma unroll
-          for (int k = 0; k < kMaxF4; ++k) {
+          for (int k = 0; k < MF4; ++k) {
             uint32_t c = l + 32 * k;
             if (c < nf4) {
               float4 v = ld_cg_f4(rowp + 16 * c);
@@ -128,9 +129,114 @@ struct EmbApp {
       }
       float4 *o = (float4 *)(out + (uint64_t)b * dim);
 #pragma unroll
-      for (int k = 0; k < kMaxF4; ++k) {
+      for (int k = 0; k < MF4; ++k) {
         uint32_t c = l + 32 * k;
         if (c < nf4) o[c] = acc[k];
+      }
+    }
+  }
+};
+
+// ============================================================================ lookup + compute pipeline
+// The DLRM-shaped overlap experiment (Sec. 4.2 computation-to-communication ratio,
+// Sec. 4.4 "AGILE async prefetches the next epoch while computing this one").
+// Work unit = (batch t, bag b): sum-pool `pooling` rows of each of n_tables tables
+// into out[t][b][k*dim ...], then the compute phase: every output element goes through
+// `iters` fused multiply-adds x = fma(x, kFmaA, kFmaB).  Warp w takes units w, w+W, ...
+// in batch-major order.
+//   SYNC : rows are requested when summed (a miss stalls the warp), then compute.
+//   ASYNC: before gathering unit u the warp requests every page of its next unit u+W,
+//          so that fetch overlaps the gather and the compute of unit u.
+// The compute is a phase of the same launch (not a separate kernel): the emulated
+// device only runs while a library launch is resident.
+constexpr float kFmaA = 0.999755859375f;  // 1 - 2^-12
+constexpr float kFmaB = 0.0009765625f;    // 2^-10
+
+template <int MF4>
+struct PipeApp {
+  uint64_t page0;     // first page of table 0
+  uint64_t tstride;   // bytes between tables
+  uint32_t n_tables, rows, dim;
+  const int64_t *idx; // [batches][tables][bags][pooling]
+  uint32_t pooling, n_bags, n_batches, iters;
+  float *out;         // [batches][bags][tables*dim]
+  uint32_t mode;
+
+  __device__ __forceinline__ uint64_t row_page(uint32_t k, uint64_t r) const {
+    return page0 + ((uint64_t)k * tstride + r * dim * 4) / kPage;
+  }
+
+  __device__ bool prefetch_unit(const Dev &d, const AppCtx &a, uint64_t u) const {
+    uint64_t t = u / n_bags, b = u % n_bags;
+    uint32_t per = n_tables * pooling;
+    for (uint32_t base = 0; base < per; base += 32) {
+      uint32_t q = base + lane_id();
+      bool want = q < per;
+      uint32_t k = want ? q / pooling : 0, p = want ? q % pooling : 0;
+      uint64_t r = want ? (uint64_t)idx[((t * n_tables + k) * n_bags + b) * pooling + p] : 0;
+      if (want && r >= rows) {
+        set_error(d, AGILE_EINVAL);
+        want = false;
+      }
+      if (!warp_request(d, want, row_page(k, r), a.q0, false, a.deadline)) return false;
+    }
+    return true;
+  }
+
+  __device__ void run(const Dev &d, const AppCtx &a) const {
+    unsigned l = lane_id();
+    const uint32_t nf4 = dim / 4;
+    const bool async = mode == AGILE_ASYNC;
+    const uint64_t units = (uint64_t)n_batches * n_bags;
+    if (async && a.warp < units && !prefetch_unit(d, a, a.warp)) return;
+    for (uint64_t u = a.warp; u < units; u += a.n_warps) {
+      if (async && u + a.n_warps < units && !prefetch_unit(d, a, u + a.n_warps)) return;
+      uint64_t t = u / n_bags, b = u % n_bags;
+      float *o = out + u * (uint64_t)n_tables * dim;
+      for (uint32_t k = 0; k < n_tables; ++k) {
+        float4 acc[MF4];
+#pragma unroll
+        for (int c = 0; c < MF4; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int64_t *ix = idx + ((t * n_tables + k) * n_bags + b) * pooling;
+        for (uint32_t p = 0; p < pooling; ++p) {
+          uint64_t r = (uint64_t)ix[p];
+          if (r >= rows) {
+            if (l == 0) set_error(d, AGILE_EINVAL);
+            r = 0;
+          }
+          uint64_t byte = (uint64_t)k * tstride + r * dim * 4;
+          uint32_t line;
+          if (!warp_pin_page(d, page0 + byte / kPage, a.q0, a.deadline, line)) return;
+          const uint8_t *rowp = line_ptr(d, line) + byte % kPage;
+#pragma unroll
+          for (int c = 0; c < MF4; ++c) {
+            uint32_t cc = l + 32 * c;
+            if (cc < nf4) {
+              float4 v = ld_cg_f4(rowp + 16 * cc);
+              acc[c].x = __fadd_rn(acc[c].x, v.x);
+              acc[c].y = __fadd_rn(acc[c].y, v.y);
+              acc[c].z = __fadd_rn(acc[c].z, v.z);
+              acc[c].w = __fadd_rn(acc[c].w, v.w);
+            }
+          }
+          __syncwarp();
+          if (l == 0) cache_unpin(d, line);
+        }
+        // compute phase on this table's pooled row
+#pragma unroll
+        for (int c = 0; c < MF4; ++c) {
+          uint32_t cc = l + 32 * c;
+          if (cc < nf4) {
+            float4 v = acc[c];
+            for (uint32_t it = 0; it < iters; ++it) {
+              v.x = __fmaf_rn(v.x, kFmaA, kFmaB);
+              v.y = __fmaf_rn(v.y, kFmaA, kFmaB);
+              v.z = __fmaf_rn(v.z, kFmaA, kFmaB);
+              v.w = __fmaf_rn(v.w, kFmaA, kFmaB);
+            }
+            ((float4 *)(o + (uint64_t)k * dim))[cc] = v;
+          }
+        }
       }
     }
   }
@@ -585,7 +691,42 @@ int agile_embedding_bag(agile_ctx *c, uint64_t table_byte0, uint32_t rows, uint3
   uint32_t warps = std::min<uint32_t>(n_bags, warps_for_cache(c, 4, 32));
   uint64_t ahead = mode == AGILE_ASYNC ? c->dev.nlines / (2ull * warps) : 0;
   ahead = std::max<uint64_t>(1, std::min<uint64_t>(32, ahead * c->cfg.prefetch_depth));
-  EmbApp app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, mode, (uint32_t)ahead};
+  if (dim <= 128) {
+    EmbApp<1> app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, mode, (uint32_t)ahead};
+    return launch_engine(c, app, stream, warps);
+  }
+  if (dim <= 256) {
+    EmbApp<2> app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, mode, (uint32_t)ahead};
+    return launch_engine(c, app, stream, warps);
+  }
+  EmbApp<kMaxF4> app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, mode, (uint32_t)ahead};
+  return launch_engine(c, app, stream, warps);
+}
+
+int agile_embedding_pipeline(agile_ctx *c, uint64_t table_byte0, uint64_t table_stride, uint32_t n_tables,
+                             uint32_t rows, uint32_t dim, const int64_t *d_idx, uint32_t pooling, uint32_t n_bags,
+                             uint32_t n_batches, uint32_t compute_iters, float *d_out, uint32_t mode, void *stream) {
+  if (!c || mode > 1) return AGILE_EINVAL;
+  if (n_bags == 0 || n_batches == 0 || n_tables == 0) return AGILE_OK;
+  if (!d_idx || !d_out || pooling == 0) return AGILE_EINVAL;
+  if (dim == 0 || dim % 4 || dim * 4 > kPage || dim > 32 * 4 * kMaxF4 || kPage % (dim * 4)) return AGILE_EINVAL;
+  if (table_byte0 % kPage || table_stride % kPage || table_stride < (uint64_t)rows * dim * 4) return AGILE_EINVAL;
+  if (table_byte0 + (uint64_t)(n_tables - 1) * table_stride + (uint64_t)rows * dim * 4 > c->cfg.store_bytes)
+    return AGILE_EINVAL;
+  if (((uintptr_t)d_out) & 15) return AGILE_EINVAL;
+  uint64_t units = (uint64_t)n_batches * n_bags;
+  uint32_t per_unit = n_tables * pooling;  // pages a warp holds or requests ahead
+  // async: a warp also holds the pages it requested for its next unit; about half of a
+  // unit's rows are taken to need a line of their own
+  uint32_t warps = (uint32_t)std::min<uint64_t>(
+      units, warps_for_cache(c, mode == AGILE_ASYNC ? std::max<uint32_t>(4, per_unit / 2) : 4, 32));
+  if (dim <= 128) {
+    PipeApp<1> app{table_byte0 / kPage, table_stride, n_tables, rows, dim, d_idx, pooling, n_bags, n_batches,
+                   compute_iters, d_out, mode};
+    return launch_engine(c, app, stream, warps);
+  }
+  PipeApp<kMaxF4> app{table_byte0 / kPage, table_stride, n_tables, rows, dim, d_idx, pooling, n_bags, n_batches,
+                      compute_iters, d_out, mode};
   return launch_engine(c, app, stream, warps);
 }
 

@@ -415,10 +415,21 @@ enum Probe { P_HIT = 0, P_BUSY = 1, P_MISS = 2 };
 // Look the page up in its set.  READY/MODIFIED -> hit (case a): the reference bit is
 // set and, with `pin`, the line is pinned against eviction.  BUSY -> in flight
 // (case c).  Otherwise a miss.
+// tags of 8 ways at once: four independent 16-byte loads from L2 (one round trip);
+// every 8-byte tag is read as one access
+__device__ __forceinline__ void ld_tags8(const unsigned long long *p, uint64_t t[8]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    asm volatile("ld.global.cg.v2.u64 {%0,%1}, [%2];" : "=l"(t[2 * k]), "=l"(t[2 * k + 1]) : "l"(p + 2 * k) : "memory");
+}
+
 __device__ __forceinline__ int cache_probe(const Dev &d, uint64_t page, bool pin, uint32_t &line) {
   uint64_t base = (uint64_t)set_of(page, d.sets) * d.ways;
+  uint64_t pre[8];
+  const bool vec = d.ways == 8;  // sets of 8 ways are 64-byte aligned: read them at once
+  if (vec) ld_tags8(&d.tag[base], pre);
   for (uint32_t w = 0; w < d.ways; ++w) {
-    uint64_t t = ld_rlx64(&d.tag[base + w]);
+    uint64_t t = vec ? pre[w & 7] : ld_rlx64(&d.tag[base + w]);
     uint64_t st = tag_state(t);
     if (st == ST_INVALID || tag_page(t) != page) continue;
     line = (uint32_t)(base + w);

@@ -72,6 +72,7 @@ __global__ void set_error_kernel(Dev d, const int32_t *err) {
 //   SYNC : the row's page is requested when the warp gets to the row.
 //   ASYNC: the pages of the rows of the warp's next 32 sorted positions are requested
 //          before the rows of the current 32 are processed.
+template <int MF4>
 struct BackwardApp {
   uint64_t page0;
   uint32_t rows, dim;
@@ -108,15 +109,15 @@ struct BackwardApp {
         m &= m - 1;
         uint64_t j0 = base + t;
         uint32_t r = row_at(j0);
-        float4 acc[kMaxF4];
+        float4 acc[MF4];
 #pragma unroll
-        for (int k = 0; k < kMaxF4; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < MF4; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         for (uint64_t jj = j0; jj < n; ++jj) {
           uint64_t key = keys[jj];
           if ((uint32_t)(key >> 32) != r) break;
           const float *g = gout + (uint64_t)bag_of[(uint32_t)key] * dim;
 #pragma unroll
-          for (int k = 0; k < kMaxF4; ++k) {
+          for (int k = 0; k < MF4; ++k) {
             uint32_t c = l + 32 * k;
             if (c < nf4) {
               float4 v = *(const float4 *)(g + 4 * c);
@@ -130,7 +131,7 @@ struct BackwardApp {
         if (grad_table) {
           float4 *o = (float4 *)(grad_table + (uint64_t)r * dim);
 #pragma unroll
-          for (int k = 0; k < kMaxF4; ++k) {
+          for (int k = 0; k < MF4; ++k) {
             uint32_t c = l + 32 * k;
             if (c < nf4) o[c] = acc[k];
           }
@@ -141,7 +142,7 @@ struct BackwardApp {
           if (!warp_pin_page(d, page0 + byte / kPage, a.q0, a.deadline, line)) return;
           uint8_t *rowp = line_ptr(d, line) + byte % kPage;
 #pragma unroll
-          for (int k = 0; k < kMaxF4; ++k) {
+          for (int k = 0; k < MF4; ++k) {
             uint32_t c = l + 32 * k;
             if (c < nf4) {
               float4 t4 = ld_cg_f4(rowp + 16 * c);
@@ -204,8 +205,13 @@ int agile_embedding_bag_backward(agile_ctx *c, uint64_t table_byte0, uint32_t ro
   set_error_kernel<<<1, 32, 0, s>>>(c->dev, err);
   AGILE_CUDA_TRY(cudaGetLastError());
   if (d_grad_table) AGILE_CUDA_TRY(cudaMemsetAsync(d_grad_table, 0, (size_t)rows * dim * 4, s));
-  BackwardApp app{table_byte0 / kPage, rows, dim, keys, bag_of, n, d_grad_out, lr, d_grad_table, mode};
-  return launch_engine(c, app, stream, warps_for_cache(c, mode == AGILE_ASYNC ? 8 : 4, 32));
+  uint32_t warps = warps_for_cache(c, mode == AGILE_ASYNC ? 8 : 4, 32);
+  if (dim <= 128) {
+    BackwardApp<1> app{table_byte0 / kPage, rows, dim, keys, bag_of, n, d_grad_out, lr, d_grad_table, mode};
+    return launch_engine(c, app, stream, warps);
+  }
+  BackwardApp<kMaxF4> app{table_byte0 / kPage, rows, dim, keys, bag_of, n, d_grad_out, lr, d_grad_table, mode};
+  return launch_engine(c, app, stream, warps);
 }
 
 }  // extern "C"

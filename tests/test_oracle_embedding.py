@@ -134,3 +134,29 @@ def test_ideal_speedup_eq1():
     xs = np.linspace(0, 3, 301)
     ys = [oracle.ideal_speedup(x) for x in xs]
     assert max(ys) == 2.0 and abs(xs[int(np.argmax(ys))] - 1.0) < 1e-12
+
+
+def test_fma_chain_is_correctly_rounded_fma():
+    # x*a + b is exact in float64 for |x| in [2^-5, 2^10] (x: 24 bits, a: 13 bits, b = 2^-10),
+    # so rounding it once to float32 is the fused multiply-add by definition
+    u = synth.uniform01(12, 4000)
+    x = ((u * 2 - 1) * 2.0 ** (u * 15 - 5)).astype(np.float32)
+    x = x[np.abs(x) >= 2.0 ** -5]
+    want = (x.astype(np.float64) * oracle.FMA_A + oracle.FMA_B).astype(np.float32)
+    assert np.array_equal(oracle.fma_chain(x, 1), want)
+    y = x.copy()
+    for _ in range(6):
+        y = (y.astype(np.float64) * oracle.FMA_A + oracle.FMA_B).astype(np.float32)
+    assert np.array_equal(oracle.fma_chain(x, 6), y)
+    assert np.array_equal(oracle.fma_chain(x, 0), x)
+
+
+def test_embedding_pipeline_composes_bag_and_chain():
+    tables = [synth.table_normal(20 + k, 300, 16) for k in range(3)]
+    idx = synth.indices_uniform(30, 2 * 3 * 10 * 4, 300).reshape(2, 3, 10, 4)
+    got = oracle.embedding_pipeline(tables, idx, 4, 3)
+    off = np.arange(11, dtype=np.int64) * 4
+    for t in range(2):
+        for k in range(3):
+            want = oracle.fma_chain(oracle.embedding_bag(tables[k], idx[t, k].reshape(-1), off), 3)
+            assert np.array_equal(got[t, :, k * 16:(k + 1) * 16], want)
