@@ -17,20 +17,96 @@ namespace {
 
 constexpr int kMaxF4 = 8;  // float4 columns per lane: dim <= 32 * 4 * 8 = 1024
 
-// ============================================================================ embedding bag
-// out[b, :] = sum_{i in [off[b], off[b+1])} T[idx[i], :], FP32, indices in increasing i.
-//
-// One warp per bag; lane l accumulates the float4 columns l, l+32, ...  Rows are read
-// from the cache line with the line pinned for that one row only, so no pin is ever
-// held across a wait (Sec. 2.3.2).
-//   SYNC : each row's page is requested when the row is needed; a miss stalls the warp
-//          until it is filled (issue then stall, Sec. 4.4 "AGILE sync").
-//   ASYNC: the warp walks its bags as one stream of rows and keeps the pages of the
-//          next `ahead` rows requested: it issues them, continues with the current
-//          rows and only waits if a row's page is still in flight when it gets there
-//          (Sec. 4.4 "AGILE async": prefetch ahead of the computation).  `ahead` is
-//          sized from the cache so that rows requested ahead are not evicted before
-//          they are used.
+// Add rows [j0, j0 + k) (lane j holds row j's line `line_j` and byte offset `off`) to acc
+// in increasing j, with several rows' loads in flight at once.
+template <int MF4>
+__device__ __forceinline__ void sum_rows(const Dev &d, uint32_t j0, uint32_t k, uint32_t line, uint32_t off,
+                                         uint32_t nf4, float4 (&acc)[MF4]) {
+  unsigned l = lane_id();
+  constexpr int RB = MF4 >= 8 ? 1 : 8 / MF4;  // rows in flight: RB * MF4 float4 per lane
+  for (uint32_t jb = 0; jb < k; jb += RB) {
+    float4 v[RB][MF4];
+#pragma unroll
+    for (int jj = 0; jj < RB; ++jj) {
+      uint32_t j = j0 + jb + jj;
+      uint32_t lj = __shfl_sync(kFull, line, j & 31);
+      uint32_t oj = __shfl_sync(kFull, off, j & 31);
+      const uint8_t *rowp = line_ptr(d, lj) + oj;
+#pragma unroll
+      for (int c = 0; c < MF4; ++c) {
+        uint32_t col = l + 32 * c;
+        v[jj][c] = (jb + jj < k && col < nf4) ? ld_cg_f4(rowp + 16 * col) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int jj = 0; jj < RB; ++jj) {
+      if (jb + jj < k) {
+#pragma unroll
+        for (int c = 0; c < MF4; ++c) {
+          acc[c].x = __fadd_rn(acc[c].x, v[jj][c].x);
+          acc[c].y = __fadd_rn(acc[c].y, v[jj][c].y);
+          acc[c].z = __fadd_rn(acc[c].z, v[jj][c].z);
+          acc[c].w = __fadd_rn(acc[c].w, v[jj][c].w);
+        }
+      }
+    }
+  }
+}
+
+// Sum-pool rows begin..cnt-1 into acc, added in increasing lane order (lane j holds row
+// j's page `pg` and byte offset `off`).  Lane l adds the
+// float4 columns l, l+32, ... (MF4 of them, dim/4 in total).
+// Each round pins, in parallel, the distinct pages of the rows not yet added (one
+// probe per distinct page), adds the longest run of rows from the next one whose pages
+// are all pinned, and lets every pin go.  When the next row's page is not READY, the
+// warp requests all missing pages without waiting, then waits for and pins that one
+// page (nothing else pinned meanwhile, Sec. 2.3.2) and adds its row: every round adds
+// at least one row, whatever the set conflicts among the rows.
+template <int MF4>
+__device__ bool gather_sum(const Dev &d, const AppCtx &a, uint32_t begin, uint32_t cnt, uint64_t pg, uint32_t off,
+                           uint32_t nf4, float4 (&acc)[MF4]) {
+  unsigned l = lane_id();
+  uint32_t j0 = begin;
+  bool first = true;
+  while (j0 < cnt) {
+    bool act = l >= j0 && l < cnt;
+    unsigned grp = __match_any_sync(kFull, act ? pg : ~0ull);
+    int lead_lane = __ffs(grp) - 1;
+    bool leader = act && lead_lane == (int)l;
+    if (first) stat_warp(d, S_WARP_COALESCED, (act && !leader) ? 1u : 0u);
+    uint32_t line = 0;
+    int pr = P_MISS;
+    if (leader) pr = cache_probe(d, pg, true, line);
+    if (first) stat_warp(d, S_HITS, (leader && pr == P_HIT) ? 1u : 0u);
+    first = false;
+    bool lhit = __shfl_sync(kFull, (int)(pr == P_HIT), lead_lane & 31) != 0;
+    uint32_t myline = __shfl_sync(kFull, line, lead_lane & 31);
+    unsigned hm = __ballot_sync(kFull, act && lhit);
+    unsigned run = ~(hm >> j0);
+    uint32_t k = run ? (uint32_t)(__ffs(run) - 1) : 32u;
+    k = min(k, cnt - j0);
+    if (k) sum_rows<MF4>(d, j0, k, myline, off, nf4, acc);
+    __syncwarp();
+    if (leader && pr == P_HIT) cache_unpin(d, line);
+    if (k) {
+      j0 += k;
+      continue;
+    }
+    // row j0's page is missing: request every missing page, then wait for row j0's
+    if (!warp_request(d, leader && pr != P_HIT, pg, a.q0, false, a.deadline)) return false;
+    uint64_t pj = __shfl_sync(kFull, pg, j0 & 31);
+    uint32_t lj;
+    if (!warp_pin_page(d, pj, a.q0, a.deadline, lj)) return false;
+    uint32_t lines = __shfl_sync(kFull, myline, 0);  // placeholder value for other lanes
+    lines = (l == j0) ? lj : lines;
+    sum_rows<MF4>(d, j0, 1, lines, off, nf4, acc);
+    __syncwarp();
+    if (l == 0) cache_unpin(d, lj);
+    j0 += 1;
+  }
+  return true;
+}
+
 template <int MF4>
 struct EmbApp {
   uint64_t page0;  // first store page of the table
@@ -41,6 +117,7 @@ struct EmbApp {
   float *out;
   uint32_t mode;
   uint32_t ahead;  // rows requested ahead of the one being summed (ASYNC), 1..32
+  uint32_t group;  // rows pinned together at most (cache-sized), 1..32
 
   __device__ __forceinline__ uint64_t row_page(uint64_t r) const { return page0 + (r * dim * 4) / kPage; }
 
@@ -103,28 +180,12 @@ struct EmbApp {
           r = 0;
         }
         uint32_t cnt = (uint32_t)min((int64_t)32, e - i0);
-        for (uint32_t j = 0; j < cnt; ++j) {
-          if (async && !issue_rows(d, a, pf, 1)) return;
-          uint64_t rj = __shfl_sync(kFull, r, j);
-          uint64_t byte = rj * dim * 4;
-          uint64_t pg = page0 + byte / kPage;
-          uint32_t inpage = (uint32_t)(byte % kPage);
-          uint32_t line;
-          if (!warp_pin_page(d, pg, a.q0, a.deadline, line)) return;
-          const uint8_t *rowp = line_ptr(d, line) + inpage;
-#pragma unroll
-          for (int k = 0; k < MF4; ++k) {
-            uint32_t c = l + 32 * k;
-            if (c < nf4) {
-              float4 v = ld_cg_f4(rowp + 16 * c);
-              acc[k].x = __fadd_rn(acc[k].x, v.x);
-              acc[k].y = __fadd_rn(acc[k].y, v.y);
-              acc[k].z = __fadd_rn(acc[k].z, v.z);
-              acc[k].w = __fadd_rn(acc[k].w, v.w);
-            }
-          }
-          __syncwarp();
-          if (l == 0) cache_unpin(d, line);
+        uint64_t byte = r * dim * 4;
+        for (uint32_t g0 = 0; g0 < cnt; g0 += group) {
+          uint32_t g1 = min(cnt, g0 + group);
+          // keep the pages of the next `ahead` rows of the stream requested
+          if (async && !issue_rows(d, a, pf, g1 - g0)) return;
+          if (!gather_sum<MF4>(d, a, g0, g1, page0 + byte / kPage, (uint32_t)(byte % kPage), nf4, acc)) return;
         }
       }
       float4 *o = (float4 *)(out + (uint64_t)b * dim);
@@ -161,6 +222,7 @@ struct PipeApp {
   uint32_t pooling, n_bags, n_batches, iters;
   float *out;         // [batches][bags][tables*dim]
   uint32_t mode;
+  uint32_t group;     // rows pinned together at most (cache-sized), 1..32
 
   __device__ __forceinline__ uint64_t row_page(uint32_t k, uint64_t r) const {
     return page0 + ((uint64_t)k * tstride + r * dim * 4) / kPage;
@@ -198,29 +260,18 @@ struct PipeApp {
 #pragma unroll
         for (int c = 0; c < MF4; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
         const int64_t *ix = idx + ((t * n_tables + k) * n_bags + b) * pooling;
-        for (uint32_t p = 0; p < pooling; ++p) {
-          uint64_t r = (uint64_t)ix[p];
+        for (uint32_t p0 = 0; p0 < pooling; p0 += 32) {
+          uint32_t cnt = min(32u, pooling - p0);
+          uint64_t r = l < cnt ? (uint64_t)ix[p0 + l] : 0;
           if (r >= rows) {
-            if (l == 0) set_error(d, AGILE_EINVAL);
+            set_error(d, AGILE_EINVAL);
             r = 0;
           }
           uint64_t byte = (uint64_t)k * tstride + r * dim * 4;
-          uint32_t line;
-          if (!warp_pin_page(d, page0 + byte / kPage, a.q0, a.deadline, line)) return;
-          const uint8_t *rowp = line_ptr(d, line) + byte % kPage;
-#pragma unroll
-          for (int c = 0; c < MF4; ++c) {
-            uint32_t cc = l + 32 * c;
-            if (cc < nf4) {
-              float4 v = ld_cg_f4(rowp + 16 * cc);
-              acc[c].x = __fadd_rn(acc[c].x, v.x);
-              acc[c].y = __fadd_rn(acc[c].y, v.y);
-              acc[c].z = __fadd_rn(acc[c].z, v.z);
-              acc[c].w = __fadd_rn(acc[c].w, v.w);
-            }
+          for (uint32_t g0 = 0; g0 < cnt; g0 += group) {
+            uint32_t g1 = min(cnt, g0 + group);
+            if (!gather_sum<MF4>(d, a, g0, g1, page0 + byte / kPage, (uint32_t)(byte % kPage), nf4, acc)) return;
           }
-          __syncwarp();
-          if (l == 0) cache_unpin(d, line);
         }
         // compute phase on this table's pooled row
 #pragma unroll
@@ -612,6 +663,13 @@ __global__ void bfs_init_kernel(int32_t *level, uint32_t n, int32_t src) {
   if (i < n) level[i] = (i == (uint64_t)src) ? 0 : -1;
 }
 
+// rows a warp pins together: with `warps` warps each holding that many lines at once,
+// at most half of the cache is pinned
+uint32_t pin_group(const agile_ctx *c, uint32_t warps) {
+  uint64_t g = c->dev.nlines / (2ull * std::max<uint32_t>(1, warps));
+  return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(32, g));
+}
+
 int bfs_check(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_t n_vertices, int32_t src,
               int32_t *d_level, uint32_t mode) {
   if (!c || mode > 1 || !d_level) return AGILE_EINVAL;
@@ -691,15 +749,16 @@ int agile_embedding_bag(agile_ctx *c, uint64_t table_byte0, uint32_t rows, uint3
   uint32_t warps = std::min<uint32_t>(n_bags, warps_for_cache(c, 4, 32));
   uint64_t ahead = mode == AGILE_ASYNC ? c->dev.nlines / (2ull * warps) : 0;
   ahead = std::max<uint64_t>(1, std::min<uint64_t>(32, ahead * c->cfg.prefetch_depth));
+  uint32_t group = pin_group(c, warps);
   if (dim <= 128) {
-    EmbApp<1> app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, mode, (uint32_t)ahead};
+    EmbApp<1> app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, mode, (uint32_t)ahead, group};
     return launch_engine(c, app, stream, warps);
   }
   if (dim <= 256) {
-    EmbApp<2> app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, mode, (uint32_t)ahead};
+    EmbApp<2> app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, mode, (uint32_t)ahead, group};
     return launch_engine(c, app, stream, warps);
   }
-  EmbApp<kMaxF4> app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, mode, (uint32_t)ahead};
+  EmbApp<kMaxF4> app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, mode, (uint32_t)ahead, group};
   return launch_engine(c, app, stream, warps);
 }
 
@@ -720,13 +779,14 @@ int agile_embedding_pipeline(agile_ctx *c, uint64_t table_byte0, uint64_t table_
   // unit's rows are taken to need a line of their own
   uint32_t warps = (uint32_t)std::min<uint64_t>(
       units, warps_for_cache(c, mode == AGILE_ASYNC ? std::max<uint32_t>(4, per_unit / 2) : 4, 32));
+  uint32_t group = pin_group(c, warps);
   if (dim <= 128) {
     PipeApp<1> app{table_byte0 / kPage, table_stride, n_tables, rows, dim, d_idx, pooling, n_bags, n_batches,
-                   compute_iters, d_out, mode};
+                   compute_iters, d_out, mode, group};
     return launch_engine(c, app, stream, warps);
   }
   PipeApp<kMaxF4> app{table_byte0 / kPage, table_stride, n_tables, rows, dim, d_idx, pooling, n_bags, n_batches,
-                      compute_iters, d_out, mode};
+                      compute_iters, d_out, mode, group};
   return launch_engine(c, app, stream, warps);
 }
 
