@@ -233,6 +233,41 @@ AGILE_API int agile_bfs_noalloc(agile_ctx *ctx, uint64_t offsets_byte0, uint64_t
                                 uint32_t n_vertices, uint64_t n_cols, int32_t src, int32_t *d_level,
                                 uint64_t *d_edges_scanned, uint32_t mode, void *stream);
 
+/* Serving loop: continuous batching of lookup requests (serving extension of the
+ * Sec. 4.4 lookups).  agile_serve_start launches one long-running call on `stream`
+ * that keeps the queues, the emulated device and the cache resident for up to
+ * session_ns (0 = 60 s); requests submitted meanwhile are admitted when the free
+ * cache-line and queue-slot budget covers them and are served alongside the requests
+ * already running.  A request is one sum-pooled embedding bag exactly as computed by
+ * agile_embedding_bag (same result alone or in any mix); its device buffers must be
+ * written before it is submitted and left alone until it completes; dim <= 128.
+ * While a session runs its kernel occupies every SM: launch no other kernel on the
+ * device until agile_serve_stop returns (copies on other streams are fine). */
+typedef struct {
+  uint64_t table_byte0;     /* table at this byte offset of the store (multiple of 4096) */
+  uint32_t rows, dim;
+  const int64_t *d_idx;     /* row numbers                                           */
+  const int64_t *d_offsets; /* n_bags + 1 bag boundaries                             */
+  uint32_t n_bags;
+  float *d_out;             /* n_bags * dim floats, 16-byte aligned                   */
+} agile_lookup_req;
+typedef struct agile_server agile_server;
+/* ring_slots: requests that may be submitted and not yet finished. */
+AGILE_API int agile_serve_start(agile_ctx *ctx, uint32_t ring_slots, uint32_t mode, uint64_t session_ns,
+                                void *stream, agile_server **out);
+/* Non-blocking; AGILE_EAGAIN when the ring is full.  *seq_out = the request's number. */
+AGILE_API int agile_serve_submit(agile_server *srv, const agile_lookup_req *req, uint64_t *seq_out);
+/* 1 when request `seq` has finished, 0 when not yet. */
+AGILE_API int agile_serve_poll(agile_server *srv, uint64_t seq);
+/* Finish every submitted request, end the session, free the server. */
+AGILE_API int agile_serve_stop(agile_server *srv);
+/* Replay a trace: request i is submitted at arrival_ns[i] (nanoseconds from the start,
+ * non-decreasing); latency_ns[i] receives the time from its arrival to its completion
+ * seen on the host.  Starts and stops its own session. */
+AGILE_API int agile_serve_replay(agile_ctx *ctx, const agile_lookup_req *reqs, uint32_t n,
+                                 const uint64_t *arrival_ns, uint64_t *latency_ns, uint32_t mode,
+                                 void *stream);
+
 /* Validation entry point: serve store pages d_pages[0..n) one at a time, in order, by
  * a single GPU thread (sync mode), and write the outcome of each request to
  * d_codes[i] (0 hit, 1 fill of an INVALID way, 2 eviction of a READY line, 3

@@ -36,7 +36,8 @@ EXPORTED = [
     "agile_store_read", "agile_read_async", "agile_write_async", "agile_wait",
     "agile_prefetch", "agile_flush", "agile_invalidate", "agile_embedding_bag",
     "agile_embedding_bag_backward", "agile_embedding_pipeline", "agile_bfs",
-    "agile_bfs_noalloc",
+    "agile_bfs_noalloc", "agile_serve_start", "agile_serve_submit", "agile_serve_poll",
+    "agile_serve_stop", "agile_serve_replay",
     "agile_cache_replay", "agile_cache_tags", "agile_cache_lines", "agile_cache_sets",
     "agile_stats", "agile_reset_stats", "agile_check", "agile_launch_shape", "agile_strerror",
 ]
@@ -68,6 +69,18 @@ STAT_FIELDS = [
     "writebacks", "eagain", "sq_full", "doorbells", "commands", "cqes", "cq_doorbells",
     "io_errors", "bytes_read", "bytes_written", "prefetches", "timeouts",
 ]
+
+
+class agile_lookup_req(C.Structure):
+    _fields_ = [
+        ("table_byte0", C.c_uint64),
+        ("rows", C.c_uint32),
+        ("dim", C.c_uint32),
+        ("d_idx", C.c_void_p),
+        ("d_offsets", C.c_void_p),
+        ("n_bags", C.c_uint32),
+        ("d_out", C.c_void_p),
+    ]
 
 
 class agile_stats_t(C.Structure):
@@ -121,6 +134,11 @@ def lib():
             "agile_reset_stats": (C.c_int, [vp]),
             "agile_check": (C.c_int, [vp]),
             "agile_launch_shape": (C.c_int, [vp, C.POINTER(u32), C.POINTER(u32)]),
+            "agile_serve_start": (C.c_int, [vp, u32, u32, u64, vp, C.POINTER(vp)]),
+            "agile_serve_submit": (C.c_int, [vp, C.POINTER(agile_lookup_req), C.POINTER(u64)]),
+            "agile_serve_poll": (C.c_int, [vp, u64]),
+            "agile_serve_stop": (C.c_int, [vp]),
+            "agile_serve_replay": (C.c_int, [vp, C.POINTER(agile_lookup_req), u32, vp, vp, u32, vp]),
             "agile_strerror": (C.c_char_p, [C.c_int]),
         }
         for name, (res, args) in sig.items():
@@ -225,6 +243,39 @@ def agile_bfs_noalloc(ctx, offsets_byte0, cols_byte0, n_vertices, n_cols, src, d
     """BFS that allocates nothing during the call (scratch in a fixed device array)."""
     return _ok(lib().agile_bfs_noalloc(ctx, offsets_byte0, cols_byte0, n_vertices, n_cols, src, d_level,
                                        d_edges, mode, stream), "agile_bfs_noalloc")
+
+
+def agile_serve_start(ctx, ring_slots, mode, session_ns, stream) -> int:
+    h = C.c_void_p()
+    _ok(lib().agile_serve_start(ctx, ring_slots, mode, session_ns, stream, C.byref(h)), "agile_serve_start")
+    return h.value
+
+
+def agile_serve_submit(srv, req: agile_lookup_req):
+    """Returns the request's sequence number, or None when the ring is full."""
+    q = C.c_uint64()
+    r = lib().agile_serve_submit(srv, C.byref(req), C.byref(q))
+    if r == AGILE_EAGAIN:
+        return None
+    _ok(r, "agile_serve_submit")
+    return q.value
+
+
+def agile_serve_poll(srv, seq) -> int:
+    r = lib().agile_serve_poll(srv, seq)
+    if r < 0:
+        _ok(r, "agile_serve_poll")
+    return r
+
+
+def agile_serve_stop(srv) -> int:
+    return _ok(lib().agile_serve_stop(srv), "agile_serve_stop")
+
+
+def agile_serve_replay(ctx, reqs, arrival_ns_ptr, latency_ns_ptr, mode, stream) -> int:
+    arr = (agile_lookup_req * len(reqs))(*reqs)
+    return _ok(lib().agile_serve_replay(ctx, arr, len(reqs), arrival_ns_ptr, latency_ns_ptr, mode, stream),
+               "agile_serve_replay")
 
 
 def agile_cache_replay(ctx, d_pages, n, d_codes, stream) -> int:

@@ -112,6 +112,7 @@ struct Dev {
   uint32_t prefetch_depth;
   int32_t *err_sticky;  // first error since the last agile_check
   uint32_t app_active;  // application warps that take part in this launch (0 = all)
+  uint64_t session_ns;  // length of a long-running launch (serving loop); 0 = timeout_ns
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -708,6 +709,105 @@ static __device__ bool warp_pin_page(const Dev &d, uint64_t page, uint32_t q0, u
   }
 }
 
+// what an application warp knows about its launch
+struct AppCtx {
+  uint32_t warp;     // app warp index in [0, n_warps)
+  uint32_t n_warps;  // app warps in the grid
+  uint32_t q0;       // this lane's home queue (Sec. 3.3.1: by thread index)
+  uint64_t deadline;
+};
+
+// Add rows [j0, j0 + k) (lane j holds row j's line `line_j` and byte offset `off`) to acc
+// in increasing j, with several rows' loads in flight at once.
+template <int MF4>
+__device__ __forceinline__ void sum_rows(const Dev &d, uint32_t j0, uint32_t k, uint32_t line, uint32_t off,
+                                         uint32_t nf4, float4 (&acc)[MF4]) {
+  unsigned l = lane_id();
+  constexpr int RB = MF4 >= 8 ? 1 : 8 / MF4;  // rows in flight: RB * MF4 float4 per lane
+  for (uint32_t jb = 0; jb < k; jb += RB) {
+    float4 v[RB][MF4];
+#pragma unroll
+    for (int jj = 0; jj < RB; ++jj) {
+      uint32_t j = j0 + jb + jj;
+      uint32_t lj = __shfl_sync(kFull, line, j & 31);
+      uint32_t oj = __shfl_sync(kFull, off, j & 31);
+      const uint8_t *rowp = line_ptr(d, lj) + oj;
+#pragma unroll
+      for (int c = 0; c < MF4; ++c) {
+        uint32_t col = l + 32 * c;
+        v[jj][c] = (jb + jj < k && col < nf4) ? ld_cg_f4(rowp + 16 * col) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int jj = 0; jj < RB; ++jj) {
+      if (jb + jj < k) {
+#pragma unroll
+        for (int c = 0; c < MF4; ++c) {
+          acc[c].x = __fadd_rn(acc[c].x, v[jj][c].x);
+          acc[c].y = __fadd_rn(acc[c].y, v[jj][c].y);
+          acc[c].z = __fadd_rn(acc[c].z, v[jj][c].z);
+          acc[c].w = __fadd_rn(acc[c].w, v[jj][c].w);
+        }
+      }
+    }
+  }
+}
+
+// Sum-pool rows begin..cnt-1 into acc, added in increasing lane order (lane j holds row
+// j's page `pg` and byte offset `off`).  Lane l adds the
+// float4 columns l, l+32, ... (MF4 of them, dim/4 in total).
+// Each round pins, in parallel, the distinct pages of the rows not yet added (one
+// probe per distinct page), adds the longest run of rows from the next one whose pages
+// are all pinned, and lets every pin go.  When the next row's page is not READY, the
+// warp requests all missing pages without waiting, then waits for and pins that one
+// page (nothing else pinned meanwhile, Sec. 2.3.2) and adds its row: every round adds
+// at least one row, whatever the set conflicts among the rows.
+template <int MF4>
+static __device__ bool gather_sum(const Dev &d, const AppCtx &a, uint32_t begin, uint32_t cnt, uint64_t pg, uint32_t off,
+                           uint32_t nf4, float4 (&acc)[MF4]) {
+  unsigned l = lane_id();
+  uint32_t j0 = begin;
+  bool first = true;
+  while (j0 < cnt) {
+    bool act = l >= j0 && l < cnt;
+    unsigned grp = __match_any_sync(kFull, act ? pg : ~0ull);
+    int lead_lane = __ffs(grp) - 1;
+    bool leader = act && lead_lane == (int)l;
+    if (first) stat_warp(d, S_WARP_COALESCED, (act && !leader) ? 1u : 0u);
+    uint32_t line = 0;
+    int pr = P_MISS;
+    if (leader) pr = cache_probe(d, pg, true, line);
+    if (first) stat_warp(d, S_HITS, (leader && pr == P_HIT) ? 1u : 0u);
+    first = false;
+    bool lhit = __shfl_sync(kFull, (int)(pr == P_HIT), lead_lane & 31) != 0;
+    uint32_t myline = __shfl_sync(kFull, line, lead_lane & 31);
+    unsigned hm = __ballot_sync(kFull, act && lhit);
+    unsigned run = ~(hm >> j0);
+    uint32_t k = run ? (uint32_t)(__ffs(run) - 1) : 32u;
+    k = min(k, cnt - j0);
+    if (k) sum_rows<MF4>(d, j0, k, myline, off, nf4, acc);
+    __syncwarp();
+    if (leader && pr == P_HIT) cache_unpin(d, line);
+    if (k) {
+      j0 += k;
+      continue;
+    }
+    // row j0's page is missing: request every missing page, then wait for row j0's
+    if (!warp_request(d, leader && pr != P_HIT, pg, a.q0, false, a.deadline)) return false;
+    uint64_t pj = __shfl_sync(kFull, pg, j0 & 31);
+    uint32_t lj;
+    if (!warp_pin_page(d, pj, a.q0, a.deadline, lj)) return false;
+    uint32_t lines = __shfl_sync(kFull, myline, 0);  // placeholder value for other lanes
+    lines = (l == j0) ? lj : lines;
+    sum_rows<MF4>(d, j0, 1, lines, off, nf4, acc);
+    __syncwarp();
+    if (l == 0) cache_unpin(d, lj);
+    j0 += 1;
+  }
+  return true;
+}
+
+
 // ================================================================ completion side
 // Release what a completed command held (Sec. 3.2.1): the line becomes READY (or
 // INVALID on an error), the share-table entry is removed, the transaction barrier
@@ -1022,18 +1122,12 @@ static __device__ bool app_barrier(const Dev &d, uint32_t n_app, uint64_t deadli
   return ok;
 }
 
-struct AppCtx {
-  uint32_t warp;     // app warp index in [0, n_warps)
-  uint32_t n_warps;  // app warps in the grid
-  uint32_t q0;       // this lane's home queue (Sec. 3.3.1: by thread index)
-  uint64_t deadline;
-};
 
 template <class App>
 __global__ void __launch_bounds__(kThreads, 2) engine_kernel(Dev d, App app) {
   uint32_t warp = threadIdx.x >> 5;
   uint32_t n_app = gridDim.x * (kWarps - 1);
-  uint64_t deadline = gtimer() + d.timeout_ns;
+  uint64_t deadline = gtimer() + (d.session_ns ? d.session_ns : d.timeout_ns);
   if (warp == 0) {
     service_loop(d, n_app, deadline + d.timeout_ns);
     return;
