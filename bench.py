@@ -393,6 +393,173 @@ def run_embedding(args, torch, ag, dev, rank, world):
             "workload": EMB_WORKLOAD}
 
 
+def fill_tables(ag, ctx, n_tables, rows, dim, stride, chunk_rows=1 << 20):
+    """Dyadic tables T_k[r, d] = ((r*131 + d*7 + k) mod 1024)/64 - 8 written in chunks."""
+    d = np.arange(dim, dtype=np.int64)[None, :]
+    for k in range(n_tables):
+        for r0 in range(0, rows, chunk_rows):
+            r = np.arange(r0, min(rows, r0 + chunk_rows), dtype=np.int64)[:, None]
+            blk = (((r * 131 + d * 7 + k) % 1024).astype(np.float32) / np.float32(64.0) - np.float32(8.0))
+            ag.agile_store_write(ctx, k * stride + r0 * dim * 4, blk.ctypes.data, blk.nbytes)
+
+
+def timed(torch, fn):
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    fn()
+    b.record()
+    b.synchronize()
+    return a.elapsed_time(b)
+
+
+def run_dlrm(args, torch, ag, dev):
+    """DLRM-shaped tables: 8 x 10M x 64 FP32 (20.48 GB) on the store, 4 GiB cache, Zipf
+    1.05 rows.  (a) overlap sweep: 2048 bags x pooling 32 per table and batch, followed by
+    the FP32 compute phase sized to r x the sync I/O time, sync vs async, both with the
+    same application warps: 32 (one block of 1,024 threads, as in the paper's CTC
+    experiment) and the full grid.  (b) serving: Poisson arrivals of requests with 1-4096
+    bags (log-uniform) x pooling 1-64 at 0.5 / 0.8 / 0.95 of the measured capacity."""
+    nt, rows, dim, nbags, pool = 8, 10_000_000, 64, 2048, 32
+    stride = round_page(rows * dim * 4)
+    res = {"workload": "8 x 10,000,000 x 64 FP32 tables (20.48 GB), 4 GiB 8-way cache, Zipf 1.05"}
+    stream = torch.cuda.current_stream().cuda_stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    t0 = time.perf_counter()
+    cfg = ag.agile_config_default(store_bytes=stride * nt, cache_bytes=4 << 30, ways=8,
+                                  device=torch.cuda.current_device(), wait_timeout_ns=60_000_000_000)
+    ctx = ag.agile_init(cfg)
+    try:
+        fill_tables(ag, ctx, nt, rows, dim, stride)
+        res["setup_s"] = round(time.perf_counter() - t0, 1)
+        zipf = synth.Zipf(rows, 1.05, permute=True, seed=4)
+        sweep = {}
+        for appw, batches in ((32, 1), (0, 4)):
+            ag.agile_config_parallelism(ctx, appw)
+            idx = zipf.rows(5, batches * nt * nbags * pool).reshape(batches, nt, nbags, pool)
+            d_idx = torch.from_numpy(idx).to(dev)
+            out = torch.empty((batches, nbags, nt * dim), dtype=torch.float32, device=dev)
+
+            def go(mode, iters, cold=True):
+                if cold:
+                    ag.agile_invalidate(ctx, stream)
+                flush.zero_()
+                return timed(torch, lambda: ag.agile_embedding_pipeline(
+                    ctx, 0, stride, nt, rows, dim, d_idx.data_ptr(), pool, nbags, batches, iters, out.data_ptr(),
+                    mode, stream))
+            go(ag.AGILE_SYNC, 0)
+            t_io = go(ag.AGILE_SYNC, 0)
+            t_io_async = go(ag.AGILE_ASYNC, 0)
+            # compute cost per iteration on a warm cache (this batch set fits in it)
+            go(ag.AGILE_SYNC, 0, cold=False)
+            w0 = go(ag.AGILE_SYNC, 0, cold=False)
+            w1 = go(ag.AGILE_SYNC, 2000, cold=False)
+            per_iter = max(1e-9, (w1 - w0) / 2000)
+            pts = []
+            for r in (0.25, 0.5, 1, 2, 4, 8):
+                iters = max(1, int(r * t_io / per_iter))
+                ts = go(ag.AGILE_SYNC, iters)
+                ta = go(ag.AGILE_ASYNC, iters)
+                pts.append({"ctc": r, "iters": iters, "sync_ms": round(ts, 3), "async_ms": round(ta, 3),
+                            "speedup": round(ts / ta, 3), "eq1_bound": round(1 + r if r <= 1 else 1 + 1 / r, 3)})
+            err = ag.agile_check(ctx)
+            look = batches * nt * nbags * pool
+            sweep["app_warps_32" if appw == 32 else "full_grid"] = {
+                "lookups": look, "io_sync_ms": round(t_io, 3), "io_async_ms": round(t_io_async, 3),
+                "io_sync_lookups_per_s": look / (t_io * 1e-3), "warm_lookups_per_s": look / (w0 * 1e-3),
+                "points": pts, "error": err}
+        ag.agile_config_parallelism(ctx, 0)
+        res["overlap"] = sweep
+        res["serving"] = run_serving(torch, ag, dev, ctx, nt, rows, dim, stride, stream)
+    finally:
+        if ctx is not None:
+            ag.agile_destroy(ctx)
+    return res
+
+
+def run_serving(torch, ag, dev, ctx, nt, rows, dim, stride, stream, n_req=600):
+    sizes = np.minimum(4096, np.maximum(1, np.round(2.0 ** (synth.uniform01(7, n_req) * 12)))).astype(int)
+    pools = synth.uniform_int(8, n_req, 64) + 1
+    which = synth.uniform_int(9, n_req, nt)
+    zipf = synth.Zipf(rows, 1.05, permute=True, seed=4)
+    keep, reqs = [], []
+    lookups = 0
+    for i in range(n_req):
+        nb, pool, k = int(sizes[i]), int(pools[i]), int(which[i])
+        d_idx = torch.from_numpy(zipf.rows(1000 + i, nb * pool)).to(dev)
+        d_off = torch.from_numpy(synth.bags_fixed(nb, pool)).to(dev)
+        out = torch.empty((nb, dim), dtype=torch.float32, device=dev)
+        keep.append((d_idx, d_off, out))
+        reqs.append(ag.agile_lookup_req(k * stride, rows, dim, d_idx.data_ptr(), d_off.data_ptr(), nb, out.data_ptr()))
+        lookups += nb * pool
+    res = {"requests": n_req, "lookups": lookups,
+           "requests_shape": "bags log-uniform 1-4096, pooling uniform 1-64, 8 tables, Zipf 1.05"}
+    for mode, name in ((ag.AGILE_SYNC, "sync"), (ag.AGILE_ASYNC, "async")):
+        lat = np.zeros(n_req, dtype=np.uint64)
+        zero = np.zeros(n_req, dtype=np.uint64)
+        t = time.perf_counter()
+        ag.agile_serve_replay(ctx, reqs, zero.ctypes.data, lat.ctypes.data, mode, stream)
+        cap = lookups / (time.perf_counter() - t)
+        pts = []
+        for lam in (0.5, 0.8, 0.95):
+            gaps = -np.log1p(-synth.uniform01(11, n_req)) * (lookups / n_req) / (lam * cap) * 1e9
+            arrival = np.cumsum(gaps).astype(np.uint64)
+            lat = np.zeros(n_req, dtype=np.uint64)
+            t = time.perf_counter()
+            ag.agile_serve_replay(ctx, reqs, arrival.ctypes.data, lat.ctypes.data, mode, stream)
+            wall = time.perf_counter() - t
+            pts.append({"load": lam, "p50_us": float(np.percentile(lat, 50) / 1e3),
+                        "p99_us": float(np.percentile(lat, 99) / 1e3), "lookups_per_s": lookups / wall})
+        res[name] = {"capacity_lookups_per_s": cap, "points": pts}
+    res["error"] = ag.agile_check(ctx)
+    return res
+
+
+def run_train(args, torch, ag, dev):
+    """Differentiable embedding bag: 4 FP32 tables of 2^22 x 128 (8 GiB) on the store,
+    2 GiB cache, Zipf 1.1 rows, batch 4096 x pooling 20; one step = forward of the 4
+    tables, backward with the fused SGD step (lr 2^-6) into the cached pages, flush."""
+    nt, rows, dim, nb, pool = 4, 1 << 22, 128, 4096, 20
+    stride = round_page(rows * dim * 4)
+    stream = torch.cuda.current_stream().cuda_stream
+    cfg = ag.agile_config_default(store_bytes=stride * nt, cache_bytes=2 << 30, ways=8,
+                                  device=torch.cuda.current_device(), wait_timeout_ns=60_000_000_000)
+    ctx = ag.agile_init(cfg)
+    res = {"workload": "4 x 4,194,304 x 128 FP32 tables (8 GiB), 2 GiB cache, Zipf 1.1, batch 4096 x pooling 20, "
+                       "forward + backward + SGD + flush"}
+    try:
+        fill_tables(ag, ctx, nt, rows, dim, stride)
+        zipf = synth.Zipf(rows, 1.1, permute=True, seed=6)
+        off = torch.from_numpy(synth.bags_fixed(nb, pool)).to(dev)
+        out = torch.empty((nb, dim), dtype=torch.float32, device=dev)
+        gout = torch.from_numpy(synth.table_normal(12, nb, dim)).to(dev)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        for mode, name in ((ag.AGILE_SYNC, "sync"), (ag.AGILE_ASYNC, "async")):
+            steps = 3 + args.warmup
+            ms = 0.0
+            for st in range(steps):
+                idx = [torch.from_numpy(zipf.rows(100 * st + k, nb * pool)).to(dev) for k in range(nt)]
+                flush.zero_()
+
+                def step():
+                    for k in range(nt):
+                        ag.agile_embedding_bag(ctx, k * stride, rows, dim, idx[k].data_ptr(), off.data_ptr(), nb,
+                                               out.data_ptr(), mode, stream)
+                        ag.agile_embedding_bag_backward(ctx, k * stride, rows, dim, idx[k].data_ptr(), off.data_ptr(),
+                                                        nb, nb * pool, gout.data_ptr(), 2.0 ** -6, 0, mode, stream)
+                    ag.agile_flush(ctx, stream)
+                t = timed(torch, step)
+                if st >= args.warmup:
+                    ms += t
+            k_steps = steps - args.warmup
+            res[name] = {"ms_per_step": ms / k_steps, "lookups_per_s": 2 * nt * nb * pool * k_steps / (ms * 1e-3)}
+        st = ag.agile_stats(ctx)
+        res["writebacks"] = st["writebacks"]
+        res["error"] = ag.agile_check(ctx)
+    finally:
+        ag.agile_destroy(ctx)
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -429,6 +596,8 @@ def main():
         res, graph = run_bfs(args, torch, ag, dev, rank, world)
         if not args.no_extras:
             res["embedding_bag"] = run_embedding(args, torch, ag, dev, rank, world)
+            res["dlrm"] = run_dlrm(args, torch, ag, dev)
+            res["train"] = run_train(args, torch, ag, dev)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline_bfs(*graph)
     else:

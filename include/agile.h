@@ -290,6 +290,10 @@ AGILE_API int agile_reset_stats(agile_ctx *ctx);
  * last agile_check (0 if none), clearing it. */
 AGILE_API int agile_check(agile_ctx *ctx);
 
+/* Kernel parallelism (Listing 1 host side, configKernelParallelism): cap on the
+ * application warps of the following calls (0 = sized from the cache per call). */
+AGILE_API int agile_config_parallelism(agile_ctx *ctx, uint32_t app_warps);
+
 /* Grid used by the library's kernels: CTAs per launch and threads per CTA. */
 AGILE_API int agile_launch_shape(agile_ctx *ctx, uint32_t *ctas, uint32_t *threads);
 

@@ -40,6 +40,7 @@ EXPORTED = [
     "agile_serve_stop", "agile_serve_replay",
     "agile_cache_replay", "agile_cache_tags", "agile_cache_lines", "agile_cache_sets",
     "agile_stats", "agile_reset_stats", "agile_check", "agile_launch_shape", "agile_strerror",
+    "agile_config_parallelism",
 ]
 
 
@@ -134,6 +135,7 @@ def lib():
             "agile_reset_stats": (C.c_int, [vp]),
             "agile_check": (C.c_int, [vp]),
             "agile_launch_shape": (C.c_int, [vp, C.POINTER(u32), C.POINTER(u32)]),
+            "agile_config_parallelism": (C.c_int, [vp, u32]),
             "agile_serve_start": (C.c_int, [vp, u32, u32, u64, vp, C.POINTER(vp)]),
             "agile_serve_submit": (C.c_int, [vp, C.POINTER(agile_lookup_req), C.POINTER(u64)]),
             "agile_serve_poll": (C.c_int, [vp, u64]),
@@ -307,6 +309,10 @@ def agile_reset_stats(ctx) -> int:
 def agile_check(ctx) -> int:
     """Device-side error since the last check (0 if none); does not raise."""
     return int(lib().agile_check(ctx))
+
+
+def agile_config_parallelism(ctx, app_warps) -> int:
+    return _ok(lib().agile_config_parallelism(ctx, app_warps), "agile_config_parallelism")
 
 
 def agile_launch_shape(ctx):

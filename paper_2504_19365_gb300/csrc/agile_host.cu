@@ -642,6 +642,12 @@ int agile_check(agile_ctx *c) {
   return e ? -e : AGILE_OK;
 }
 
+int agile_config_parallelism(agile_ctx *c, uint32_t app_warps) {
+  if (!c) return AGILE_EINVAL;
+  c->cfg.app_warps = app_warps;
+  return AGILE_OK;
+}
+
 int agile_launch_shape(agile_ctx *c, uint32_t *ctas, uint32_t *threads) {
   if (!c) return AGILE_EINVAL;
   if (ctas) *ctas = (uint32_t)engine_grid<ReadApp>(c);
