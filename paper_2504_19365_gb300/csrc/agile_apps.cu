@@ -17,8 +17,9 @@ namespace {
 
 constexpr int kMaxF4 = 8;  // float4 columns per lane: dim <= 32 * 4 * 8 = 1024
 
-template <int MF4>
+template <int MF4, int MinBlocks = 2>
 struct EmbApp {
+  static constexpr int kMinBlocks = MinBlocks;  // CTAs per SM the kernel is compiled for
   uint64_t page0;  // first store page of the table
   uint32_t rows, dim;
   const int64_t *idx;
@@ -70,6 +71,92 @@ struct EmbApp {
     return true;
   }
 
+  // A bag of at most `group` rows (one row per lane) prepared for the fast path: its
+  // pages probed and pinned (one probe per distinct page) without waiting.  ok = every
+  // page was READY and is now pinned.
+  struct Prep {
+    uint32_t b, cnt;
+    bool fast, ok, leader;
+    uint64_t pg;
+    uint32_t off, line, myline;
+  };
+
+  __device__ void prep(const Dev &d, uint32_t b, Prep &p) const {
+    unsigned l = lane_id();
+    p.b = b;
+    p.cnt = 0;
+    p.fast = p.ok = p.leader = false;
+    if (b >= n_bags) return;
+    int64_t s = off[b], e = off[b + 1];
+    p.cnt = (uint32_t)(e - s);
+    p.fast = e > s && e - s <= (int64_t)min(group, 32u);
+    if (!p.fast) return;
+    bool want = l < p.cnt;
+    uint64_t r = want ? (uint64_t)idx[s + l] : 0;
+    if (want && r >= rows) {
+      set_error(d, AGILE_EINVAL);
+      r = 0;
+    }
+    uint64_t byte = r * dim * 4;
+    p.pg = page0 + byte / kPage;
+    p.off = (uint32_t)(byte % kPage);
+    unsigned grp = __match_any_sync(kFull, want ? p.pg : ~0ull);
+    int lead = __ffs(grp) - 1;
+    p.leader = want && lead == (int)l;
+    int pr = P_HIT;
+    p.line = 0;
+    if (p.leader) pr = cache_probe(d, p.pg, true, p.line);
+    p.ok = __all_sync(kFull, !p.leader || pr == P_HIT);
+    if (p.ok) {  // counted here; a bag that is not all resident is counted by gather_sum
+      stat_warp(d, S_WARP_COALESCED, (want && !p.leader) ? 1u : 0u);
+      stat_warp(d, S_HITS, p.leader ? 1u : 0u);
+    } else if (p.leader && pr == P_HIT) {
+      cache_unpin(d, p.line);  // not all resident: hold nothing, the slow path takes it
+      p.leader = false;
+    } else if (!p.ok) {
+      p.leader = false;
+    }
+    p.myline = __shfl_sync(kFull, p.line, lead & 31);
+  }
+
+  __device__ void store_out(uint32_t b, const float4 (&acc)[MF4], uint32_t nf4) const {
+    unsigned l = lane_id();
+    float4 *o = (float4 *)(out + (uint64_t)b * dim);
+#pragma unroll
+    for (int k = 0; k < MF4; ++k) {
+      uint32_t c = l + 32 * k;
+      if (c < nf4) o[c] = acc[k];
+    }
+  }
+
+  // general path for one bag: rows in groups, each group waiting for its pages as needed
+  __device__ bool slow_bag(const Dev &d, const AppCtx &a, uint32_t b, uint32_t nf4, Cursor &pf) const {
+    unsigned l = lane_id();
+    const bool async = mode == AGILE_ASYNC;
+    int64_t s = off[b], e = off[b + 1];
+    float4 acc[MF4];
+#pragma unroll
+    for (int k = 0; k < MF4; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t i0 = s; i0 < e; i0 += 32) {
+      int64_t i = i0 + l;
+      uint64_t r = i < e ? (uint64_t)idx[i] : 0;
+      if (i < e && r >= rows) {
+        set_error(d, AGILE_EINVAL);
+        r = 0;
+      }
+      uint32_t cnt = (uint32_t)min((int64_t)32, e - i0);
+      uint64_t byte = r * dim * 4;
+      for (uint32_t g0 = 0; g0 < cnt; g0 += group) {
+        uint32_t g1 = min(cnt, g0 + group);
+        // keep the pages of the next `ahead` rows of the stream requested
+        if (async && !issue_rows(d, a, pf, g1 - g0)) return false;
+        if (!gather_sum<MF4>(d, a, g0, g1, page0 + byte / kPage, (uint32_t)(byte % kPage), nf4, acc)) return false;
+      }
+    }
+    store_out(b, acc, nf4);
+    return true;
+  }
+
   __device__ void run(const Dev &d, const AppCtx &a) const {
     unsigned l = lane_id();
     const uint32_t nf4 = dim / 4;
@@ -77,34 +164,57 @@ struct EmbApp {
     Cursor pf;  // prefetch cursor, `ahead` rows in front of the summation
     cur_init(a, pf);
     if (async && !issue_rows(d, a, pf, ahead)) return;
+    constexpr int RB = MF4 >= 8 ? 1 : 8 / MF4;
+    Prep cur;
+    prep(d, a.warp, cur);
     for (uint32_t b = a.warp; b < n_bags; b += a.n_warps) {
-      int64_t s = off[b], e = off[b + 1];
+      uint32_t nb = b + a.n_warps;
+      if (!(cur.fast && cur.ok)) {
+        // nothing pinned: the general path may wait
+        if (async && cur.fast && !issue_rows(d, a, pf, cur.cnt)) return;
+        if (!slow_bag(d, a, b, nf4, pf)) return;
+        prep(d, nb, cur);
+        continue;
+      }
+      // fast path: all pages of bag b are pinned.  Issue the first rows' loads, probe and
+      // pin bag b+W while they are in flight, then add the rows in order.
+      if (async && !issue_rows(d, a, pf, cur.cnt)) return;
       float4 acc[MF4];
 #pragma unroll
       for (int k = 0; k < MF4; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int64_t i0 = s; i0 < e; i0 += 32) {
-        int64_t i = i0 + l;
-        uint64_t r = i < e ? (uint64_t)idx[i] : 0;
-        if (i < e && r >= rows) {
-          set_error(d, AGILE_EINVAL);
-          r = 0;
-        }
-        uint32_t cnt = (uint32_t)min((int64_t)32, e - i0);
-        uint64_t byte = r * dim * 4;
-        for (uint32_t g0 = 0; g0 < cnt; g0 += group) {
-          uint32_t g1 = min(cnt, g0 + group);
-          // keep the pages of the next `ahead` rows of the stream requested
-          if (async && !issue_rows(d, a, pf, g1 - g0)) return;
-          if (!gather_sum<MF4>(d, a, g0, g1, page0 + byte / kPage, (uint32_t)(byte % kPage), nf4, acc)) return;
-        }
-      }
-      float4 *o = (float4 *)(out + (uint64_t)b * dim);
+      float4 v[RB][MF4];
 #pragma unroll
-      for (int k = 0; k < MF4; ++k) {
-        uint32_t c = l + 32 * k;
-        if (c < nf4) o[c] = acc[k];
+      for (int jj = 0; jj < RB; ++jj) {
+        uint32_t lj = __shfl_sync(kFull, cur.myline, jj);
+        uint32_t oj = __shfl_sync(kFull, cur.off, jj);
+        const uint8_t *rowp = line_ptr(d, lj) + oj;
+#pragma unroll
+        for (int c = 0; c < MF4; ++c) {
+          uint32_t col = l + 32 * c;
+          v[jj][c] = ((uint32_t)jj < cur.cnt && col < nf4) ? ld_cg_f4(rowp + 16 * col) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
       }
+      Prep nxt;
+      prep(d, nb, nxt);  // never waits; pins only pages that are READY
+#pragma unroll
+      for (int jj = 0; jj < RB; ++jj) {
+        if ((uint32_t)jj < cur.cnt) {
+#pragma unroll
+          for (int c = 0; c < MF4; ++c) {
+            acc[c].x = __fadd_rn(acc[c].x, v[jj][c].x);
+            acc[c].y = __fadd_rn(acc[c].y, v[jj][c].y);
+            acc[c].z = __fadd_rn(acc[c].z, v[jj][c].z);
+            acc[c].w = __fadd_rn(acc[c].w, v[jj][c].w);
+          }
+        }
+      }
+      if (cur.cnt > (uint32_t)RB) sum_rows<MF4>(d, RB, cur.cnt - RB, cur.myline, cur.off, nf4, acc);
+      __syncwarp();
+      if (cur.leader) cache_unpin(d, cur.line);
+      store_out(b, acc, nf4);
+      cur = nxt;
     }
+    (void)l;
   }
 };
 
@@ -657,19 +767,25 @@ int agile_embedding_bag(agile_ctx *c, uint64_t table_byte0, uint32_t rows, uint3
   if (kPage % (dim * 4)) return AGILE_EINVAL;
   // one warp per bag while the rows each warp holds or requests ahead fit in the cache
   uint32_t warps = std::min<uint32_t>(n_bags, warps_for_cache(c, 4, 32));
-  uint64_t ahead = mode == AGILE_ASYNC ? c->dev.nlines / (2ull * warps) : 0;
-  ahead = std::max<uint64_t>(1, std::min<uint64_t>(32, ahead * c->cfg.prefetch_depth));
-  uint32_t group = pin_group(c, warps);
+  auto go = [&](auto tag) {
+    using App = decltype(tag);
+    // rows requested ahead (async) and pin groups are sized by the warps that run
+    uint32_t run = running_app_warps<App>(c, warps);
+    uint64_t ahead = mode == AGILE_ASYNC ? c->dev.nlines / (2ull * run) : 0;
+    ahead = std::max<uint64_t>(1, std::min<uint64_t>(32, ahead * c->cfg.prefetch_depth));
+    App app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, mode, (uint32_t)ahead,
+            pin_group(c, run)};
+    return launch_engine(c, app, stream, warps);
+  };
   if (dim <= 128) {
-    EmbApp<1> app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, mode, (uint32_t)ahead, group};
-    return launch_engine(c, app, stream, warps);
+    // three CTAs per SM (fewer registers a thread, so slower service warps) pay off only
+    // when the cache holds enough lines for more warps than two CTAs per SM give
+    uint64_t want = c->cfg.app_warps ? c->cfg.app_warps : warps;
+    if (want > (uint64_t)std::max(0, engine_grid<EmbApp<1, 2>>(c)) * (kWarps - 1)) return go(EmbApp<1, 3>{});
+    return go(EmbApp<1, 2>{});
   }
-  if (dim <= 256) {
-    EmbApp<2> app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, mode, (uint32_t)ahead, group};
-    return launch_engine(c, app, stream, warps);
-  }
-  EmbApp<kMaxF4> app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, mode, (uint32_t)ahead, group};
-  return launch_engine(c, app, stream, warps);
+  if (dim <= 256) return go(EmbApp<2>{});
+  return go(EmbApp<kMaxF4>{});
 }
 
 int agile_embedding_pipeline(agile_ctx *c, uint64_t table_byte0, uint64_t table_stride, uint32_t n_tables,
@@ -689,14 +805,13 @@ int agile_embedding_pipeline(agile_ctx *c, uint64_t table_byte0, uint64_t table_
   // unit's rows are taken to need a line of their own
   uint32_t warps = (uint32_t)std::min<uint64_t>(
       units, warps_for_cache(c, mode == AGILE_ASYNC ? std::max<uint32_t>(4, per_unit / 2) : 4, 32));
-  uint32_t group = pin_group(c, warps);
   if (dim <= 128) {
     PipeApp<1> app{table_byte0 / kPage, table_stride, n_tables, rows, dim, d_idx, pooling, n_bags, n_batches,
-                   compute_iters, d_out, mode, group};
+                   compute_iters, d_out, mode, pin_group(c, running_app_warps<PipeApp<1>>(c, warps))};
     return launch_engine(c, app, stream, warps);
   }
   PipeApp<kMaxF4> app{table_byte0 / kPage, table_stride, n_tables, rows, dim, d_idx, pooling, n_bags, n_batches,
-                      compute_iters, d_out, mode, group};
+                      compute_iters, d_out, mode, pin_group(c, running_app_warps<PipeApp<kMaxF4>>(c, warps))};
   return launch_engine(c, app, stream, warps);
 }
 

@@ -61,6 +61,15 @@ int engine_grid(agile_ctx *c) {
   return g;
 }
 
+// Application warps a launch of this instantiation runs when the call wants `active`
+// (0 = all): the context's app_warps setting overrides `active`, the grid bounds both.
+template <class App>
+uint32_t running_app_warps(agile_ctx *c, uint32_t active) {
+  uint64_t n_app = (uint64_t)std::max(0, engine_grid<App>(c)) * (kWarps - 1);
+  uint64_t want = c->cfg.app_warps ? c->cfg.app_warps : active;
+  return (uint32_t)std::max<uint64_t>(1, want && want < n_app ? want : n_app);
+}
+
 // `active`: application warps the call wants (0 = every app warp of the grid); the
 // context's app_warps setting overrides it.
 template <class App>

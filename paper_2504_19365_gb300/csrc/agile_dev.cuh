@@ -153,6 +153,11 @@ __device__ __forceinline__ void st_rlx64(unsigned long long *p, uint64_t v) {
 __device__ __forceinline__ void st_rlx32(uint32_t *p, uint32_t v) {
   asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ uint64_t atom_add_acq(unsigned long long *p, uint64_t v) {
+  uint64_t old;
+  asm volatile("atom.acquire.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+}
 __device__ __forceinline__ void fence_sc() { asm volatile("fence.sc.gpu;" ::: "memory"); }
 __device__ __forceinline__ void fence_ar() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 // 16-byte loads/stores that bypass L1: cache lines and store pages are rewritten by
@@ -183,22 +188,29 @@ __device__ __forceinline__ int64_t ld_cg_s64(const void *p) {
 }
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31; }
 
+// counters are kept in kStatShards copies (by CTA) so that warps all over the GPU do not
+// serialise on one address; the host adds the copies up
+constexpr int kStatShards = 32;
+__device__ __forceinline__ unsigned long long *stat_ptr(const Dev &d, int s) {
+  return &d.stats[(blockIdx.x % kStatShards) * S_COUNT + s];
+}
+
 __device__ __forceinline__ void stat_add(const Dev &d, int s, uint64_t v) {
-  if (v) atomicAdd(&d.stats[s], (unsigned long long)v);
+  if (v) atomicAdd(stat_ptr(d, s), (unsigned long long)v);
 }
 // warp-aggregated statistic: every lane passes its own count
 __device__ __forceinline__ void stat_warp(const Dev &d, int s, uint32_t v) {
   unsigned b = __ballot_sync(kFull, v != 0);
   if (!b) return;
   uint32_t sum = __reduce_add_sync(kFull, v);
-  if (lane_id() == 0) atomicAdd(&d.stats[s], (unsigned long long)sum);
+  if (lane_id() == 0) atomicAdd(stat_ptr(d, s), (unsigned long long)sum);
 }
 
 // record the first error of the launch and of the context
 __device__ __forceinline__ void set_error(const Dev &d, int code) {
   atomicCAS(&d.run->error, 0u, (uint32_t)(-code));
   atomicCAS((uint32_t *)d.err_sticky, 0u, (uint32_t)(-code));
-  if (code == -110) atomicAdd(&d.stats[S_TIMEOUTS], 1ull);
+  if (code == -110) atomicAdd(stat_ptr(d, S_TIMEOUTS), 1ull);
 }
 __device__ __forceinline__ bool aborted(const Dev &d) { return ld_rlx32(&d.run->error) != 0; }
 
@@ -283,7 +295,7 @@ __device__ __forceinline__ bool sq_reserve_any(const Dev &d, uint32_t q0, uint32
       return true;
     }
   }
-  atomicAdd(&d.stats[S_SQ_FULL], 1ull);
+  atomicAdd(stat_ptr(d, S_SQ_FULL), 1ull);
   return false;
 }
 
@@ -325,7 +337,7 @@ __device__ __forceinline__ void sq_move_tail(const Dev &d, uint32_t q) {
     st_rlx32(&d.sq_tail[q], t);
     fence_ar();
     st_rel32(&d.sq_db[q], t & d.dmask);
-    atomicAdd(&d.stats[S_DOORBELLS], 1ull);
+    atomicAdd(stat_ptr(d, S_DOORBELLS), 1ull);
   }
 }
 
@@ -439,11 +451,10 @@ __device__ __forceinline__ int cache_probe(const Dev &d, uint64_t page, bool pin
       if (!(t & TAG_REF)) atomicOr(&d.tag[base + w], TAG_REF);
       return P_HIT;
     }
-    uint64_t old = atomicAdd(&d.tag[base + w], PIN1);
+    uint64_t old = atom_add_acq(&d.tag[base + w], PIN1);  // line data is read after the pin
     uint64_t ost = tag_state(old);
     if (tag_page(old) == page && (ost == ST_READY || ost == ST_MODIFIED)) {
       if (!(old & TAG_REF)) atomicOr(&d.tag[base + w], TAG_REF);
-      fence_ar();  // the line data is read after the pin is observed
       return P_HIT;
     }
     atomicAdd(&d.tag[base + w], (unsigned long long)(-(int64_t)PIN1));
@@ -490,7 +501,7 @@ static __device__ int cache_miss(const Dev &d, uint64_t page, uint32_t q0, uint3
   if (fill) {
     sh = sh_insert(d, page, SH_FILL);
     if (sh < 0) {
-      atomicAdd(&d.stats[S_SHARE_RETRIES], 1ull);
+      atomicAdd(stat_ptr(d, S_SHARE_RETRIES), 1ull);
       return M_RETRY;
     }
   }
@@ -539,7 +550,7 @@ static __device__ int cache_miss(const Dev &d, uint64_t page, uint32_t q0, uint3
   }
   if (victim < 0) {
     if (fill) sh_remove(d, (uint64_t)sh);
-    atomicAdd(&d.stats[S_EAGAIN], 1ull);
+    atomicAdd(stat_ptr(d, S_EAGAIN), 1ull);
     return M_RETRY;
   }
   line = (uint32_t)(base + victim);
@@ -556,14 +567,14 @@ static __device__ int cache_miss(const Dev &d, uint64_t page, uint32_t q0, uint3
   is.slot = slot;
   is.ticket = ticket;
   is.code = wb ? 3 : (old ? 2 : 1);
-  if (old) atomicAdd(&d.stats[S_EVICTIONS], 1ull);
+  if (old) atomicAdd(stat_ptr(d, S_EVICTIONS), 1ull);
   if (wb) {
     uint8_t *stg = d.staging + ((uint64_t)q * d.depth + slot) * kPage;
     lane_copy_page(stg, line_ptr(d, line));
     fence_ar();
     sq_commit(d, q, slot, ticket, OP_WRITE, (uint64_t)stg, tag_page(old),
               ctx_make(CTX_WB, (uint32_t)sh_wb, 0));
-    atomicAdd(&d.stats[S_WRITEBACKS], 1ull);
+    atomicAdd(stat_ptr(d, S_WRITEBACKS), 1ull);
     if (!fill) return M_ISSUED;  // the write-back is the command to ring
     slot = (slot + 1) & d.dmask;
     ticket += 1;
@@ -574,7 +585,7 @@ static __device__ int cache_miss(const Dev &d, uint64_t page, uint32_t q0, uint3
   }
   sq_commit(d, q, slot, ticket, OP_READ, (uint64_t)line_ptr(d, line), page,
             ctx_make(CTX_FILL, (uint32_t)sh, line));
-  atomicAdd(&d.stats[S_MISSES], 1ull);
+  atomicAdd(stat_ptr(d, S_MISSES), 1ull);
   is.slot = slot;
   is.ticket = ticket;
   return M_ISSUED;
@@ -615,9 +626,9 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
       int pr = cache_probe(d, page, false, line);
       if (pr == P_HIT) {
         need = false;
-        if (first) atomicAdd(&d.stats[S_HITS], 1ull);
+        if (first) atomicAdd(stat_ptr(d, S_HITS), 1ull);
       } else if (pr == P_BUSY) {
-        if (first) atomicAdd(&d.stats[S_BUSY_HITS], 1ull);
+        if (first) atomicAdd(stat_ptr(d, S_BUSY_HITS), 1ull);
         if (!wait) need = false;
       } else {
         int m = cache_miss(d, page, q0, line, is);
@@ -672,11 +683,10 @@ __device__ __forceinline__ int warp_probe_pin(const Dev &d, uint64_t page, uint3
     if (tag_state(t) == ST_BUSY) {
       pr = P_BUSY;
     } else {
-      uint64_t old = atomicAdd(&d.tag[line], PIN1);
+      uint64_t old = atom_add_acq(&d.tag[line], PIN1);  // line data is read after the pin
       uint64_t ost = tag_state(old);
       if (tag_page(old) == page && (ost == ST_READY || ost == ST_MODIFIED)) {
         if (!(old & TAG_REF)) atomicOr(&d.tag[line], TAG_REF);
-        fence_ar();  // the line data is read after the pin is observed
         pr = P_HIT;
       } else {
         atomicAdd(&d.tag[line], (unsigned long long)(-(int64_t)PIN1));
@@ -697,7 +707,7 @@ static __device__ bool warp_pin_page(const Dev &d, uint64_t page, uint32_t q0, u
     int pr = warp_probe_pin(d, page, line);
     if (pr == P_HIT) {
       line_out = line;
-      if (lane_id() == 0 && round == 0) atomicAdd(&d.stats[S_HITS], 1ull);
+      if (lane_id() == 0 && round == 0) atomicAdd(stat_ptr(d, S_HITS), 1ull);
       return true;
     }
     if (!warp_request(d, lane_id() == 0, page, q0, true, deadline)) return false;
@@ -832,7 +842,7 @@ __device__ __forceinline__ void complete_command(const Dev &d, uint32_t q, uint3
     if (idx) atomicAnd(&d.tag[idx - 1], ~TAG_WB);  // flush write-back from the line itself
     sh_remove(d, sh);
   }
-  if (status) atomicAdd(&d.stats[S_IO_ERRORS], 1ull);
+  if (status) atomicAdd(stat_ptr(d, S_IO_ERRORS), 1ull);
   st_rel64(&d.cmpl[i], ((ticket & 0xFFFFFFFFull) << 32) | ((uint64_t)(status & 0x7FFF) << 1) | 1ull);
   st_rel64(&d.sqe_state[i], (ticket << 2) | SQE_EMPTY);
   atomicAdd(&d.sq_resv[q], (unsigned long long)(-(int64_t)(1ull << 32)));
@@ -881,8 +891,8 @@ static __device__ bool cq_poll(const Dev &d, uint32_t q) {
     st_rlx32(&ps[0], offset);
     st_rlx32(&ps[1], mask);
     st_rlx32(&ps[2], phase);
-    if (found) atomicAdd(&d.stats[S_CQES], (unsigned long long)found);
-    if (windows) atomicAdd(&d.stats[S_CQ_DOORBELLS], (unsigned long long)windows);
+    if (found) atomicAdd(stat_ptr(d, S_CQES), (unsigned long long)found);
+    if (windows) atomicAdd(stat_ptr(d, S_CQ_DOORBELLS), (unsigned long long)windows);
   }
   __syncwarp();
   return found != 0;
@@ -1026,9 +1036,9 @@ static __device__ uint32_t emu_serve(const Dev &d, uint32_t q) {
     }
   }
   if (l == 0) {
-    atomicAdd(&d.stats[S_COMMANDS], (unsigned long long)k);
-    if (rd) atomicAdd(&d.stats[S_BYTES_READ], (unsigned long long)rd * kPage);
-    if (wr) atomicAdd(&d.stats[S_BYTES_WRITTEN], (unsigned long long)wr * kPage);
+    atomicAdd(stat_ptr(d, S_COMMANDS), (unsigned long long)k);
+    if (rd) atomicAdd(stat_ptr(d, S_BYTES_READ), (unsigned long long)rd * kPage);
+    if (wr) atomicAdd(stat_ptr(d, S_BYTES_WRITTEN), (unsigned long long)wr * kPage);
   }
   __syncwarp();
   return k;
@@ -1123,8 +1133,19 @@ static __device__ bool app_barrier(const Dev &d, uint32_t n_app, uint64_t deadli
 }
 
 
+// CTAs per SM the engine is compiled for (register budget): App::kMinBlocks if the
+// application asks for more occupancy, else 2
+template <class App, class = void>
+struct MinBlocks {
+  static constexpr int value = 2;
+};
 template <class App>
-__global__ void __launch_bounds__(kThreads, 2) engine_kernel(Dev d, App app) {
+struct MinBlocks<App, decltype((void)App::kMinBlocks, void())> {
+  static constexpr int value = App::kMinBlocks;
+};
+
+template <class App>
+__global__ void __launch_bounds__(kThreads, MinBlocks<App>::value) engine_kernel(Dev d, App app) {
   uint32_t warp = threadIdx.x >> 5;
   uint32_t n_app = gridDim.x * (kWarps - 1);
   uint64_t deadline = gtimer() + (d.session_ns ? d.session_ns : d.timeout_ns);

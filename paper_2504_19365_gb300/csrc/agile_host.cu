@@ -172,7 +172,7 @@ struct WriteApp {
         __syncwarp();
         if (l == 0) {
           sq_commit(d, q, slot, ticket, OP_WRITE, (uint64_t)stg, page, ctx_make(CTX_WB, (uint32_t)sh, 0));
-          atomicAdd(&d.stats[S_WRITEBACKS], 1ull);
+          atomicAdd(stat_ptr(d, S_WRITEBACKS), 1ull);
         }
         if (!warp_ring(d, l == 0, q, slot, ticket, a.deadline)) return;
         t = make_token(q, slot, ticket);
@@ -240,7 +240,7 @@ struct FlushApp {
           uint8_t *stg = d.staging + ((uint64_t)q * d.depth + slot) * kPage;
           sq_commit(d, q, slot, ticket, OP_WRITE, (uint64_t)stg, tag_page(t),
                     ctx_make(CTX_WB, (uint32_t)sh, (uint32_t)(line + 1)));
-          atomicAdd(&d.stats[S_WRITEBACKS], 1ull);
+          atomicAdd(stat_ptr(d, S_WRITEBACKS), 1ull);
         }
         if (!warp_ring(d, mine, q, slot, ticket, a.deadline)) return;
       }
@@ -278,7 +278,7 @@ struct ReplayApp {
           int pr = cache_probe(d, page, false, line);
           if (pr == P_HIT) {
             done = 1;
-            atomicAdd(&d.stats[S_HITS], 1ull);
+            atomicAdd(stat_ptr(d, S_HITS), 1ull);
           } else if (pr == P_MISS) {
             int m = cache_miss(d, page, a.q0, line, is);
             if (m == M_ISSUED) {
@@ -478,7 +478,7 @@ int agile_init(const agile_config *cfg_in, agile_ctx **out) {
   d.emu_arrival = (unsigned long long *)A(Q * D * 8);
   d.staging = (uint8_t *)A(Q * D * kPage);
   d.run = (RunState *)A(sizeof(RunState));
-  d.stats = (unsigned long long *)A(S_COUNT * 8);
+  d.stats = (unsigned long long *)A((size_t)kStatShards * S_COUNT * 8);
   d.err_sticky = (int32_t *)A(16);
   if (!ok) {
     agile_destroy(c);
@@ -620,7 +620,14 @@ int agile_stats(agile_ctx *c, agile_stats_t *out) {
   static_assert(sizeof(agile_stats_t) == S_COUNT * 8, "stats layout");
   AGILE_CUDA_TRY(cudaSetDevice(c->device));
   AGILE_CUDA_TRY(cudaDeviceSynchronize());
-  AGILE_CUDA_TRY(cudaMemcpy(out, c->dev.stats, sizeof(agile_stats_t), cudaMemcpyDeviceToHost));
+  std::vector<unsigned long long> sh((size_t)kStatShards * S_COUNT);
+  AGILE_CUDA_TRY(cudaMemcpy(sh.data(), c->dev.stats, sh.size() * 8, cudaMemcpyDeviceToHost));
+  uint64_t *o = (uint64_t *)out;
+  for (int s = 0; s < S_COUNT; ++s) {
+    uint64_t v = 0;
+    for (int k = 0; k < kStatShards; ++k) v += sh[(size_t)k * S_COUNT + s];
+    o[s] = v;
+  }
   return AGILE_OK;
 }
 
@@ -628,7 +635,7 @@ int agile_reset_stats(agile_ctx *c) {
   if (!c) return AGILE_EINVAL;
   AGILE_CUDA_TRY(cudaSetDevice(c->device));
   AGILE_CUDA_TRY(cudaDeviceSynchronize());
-  AGILE_CUDA_TRY(cudaMemset(c->dev.stats, 0, S_COUNT * 8));
+  AGILE_CUDA_TRY(cudaMemset(c->dev.stats, 0, (size_t)kStatShards * S_COUNT * 8));
   return AGILE_OK;
 }
 

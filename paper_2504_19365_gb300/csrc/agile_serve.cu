@@ -275,9 +275,11 @@ int agile_serve_start(agile_ctx *c, uint32_t ring_slots, uint32_t mode, uint64_t
   AGILE_CUDA_TRY(cudaHostGetDevicePointer(&done_d, s->done, 0));
   AGILE_CUDA_TRY(cudaHostGetDevicePointer(&stop_d, s->stop, 0));
   uint32_t warps = warps_for_cache(c, 4, 32);
+  // pin groups sized by the warps that run (one of them schedules)
+  uint32_t run = running_app_warps<ServeApp>(c, warps + 1);
   ServeApp app{(ServeSlot *)ring_d, (unsigned long long *)done_d, (const uint32_t *)stop_d,
                (ServeDev *)s->dstate, (ReqState *)((ServeDev *)s->dstate + 1), ring_slots,
-               c->dev.nlines / 2, mode, std::max<uint32_t>(1, std::min<uint32_t>(32, (uint32_t)(c->dev.nlines / (2ull * warps))))};
+               c->dev.nlines / 2, mode, std::max<uint32_t>(1, std::min<uint32_t>(32, (uint32_t)(c->dev.nlines / (2ull * run))))};
   uint64_t saved = c->dev.session_ns;
   c->dev.session_ns = session_ns ? session_ns : 60ull * 1000 * 1000 * 1000;
   int r = launch_engine(c, app, stream, warps + 1);

@@ -97,3 +97,33 @@ def test_table_at_offset_and_out_of_range_index_reported():
                                ag.AGILE_SYNC, c.stream)
         torch.cuda.synchronize()
         assert ag.agile_check(c.h) == ag.AGILE_EINVAL
+
+
+@pytest.mark.parametrize("app_warps", [0, 1024])
+def test_large_cache_cold_then_warm_hits(app_warps):
+    # A cache with room for more warps than two CTAs per SM hold (the three-CTA kernel is
+    # taken by default, the two-CTA one with 1,024 app warps); bags of 0..40 rows take
+    # the all-resident path (<= 32 rows, every page pinned at once) and the general one.
+    rows, dim = 131072, 128
+    T = synth.table_normal(11, rows, dim)
+    sizes = synth.uniform_int(12, 8192, 41)
+    off = np.zeros(8193, dtype=np.int64)
+    np.cumsum(sizes, out=off[1:])
+    idx = synth.indices_uniform(13, int(off[-1]), rows)
+    want = oracle.embedding_bag(T, idx, off)
+    with Ctx(T.nbytes, cache_bytes=96 << 20, ways=8) as c:
+        c.put(0, T)
+        if app_warps:
+            ag.agile_config_parallelism(c.h, app_warps)
+        for mode in (ag.AGILE_SYNC, ag.AGILE_ASYNC):
+            ag.agile_invalidate(c.h, c.stream)
+            cold = _bag(c, 0, rows, dim, idx, off, mode)
+            ag.agile_reset_stats(c.h)
+            warm = _bag(c, 0, rows, dim, idx, off, mode)
+            st = c.stats()
+            assert np.array_equal(cold.view(np.uint32), want.view(np.uint32))
+            assert np.array_equal(warm.view(np.uint32), want.view(np.uint32))
+            assert st["misses"] == 0 and st["hits"] > 0
+            # every looked-up row was served by a probe of its own or of a warp-mate
+            assert st["hits"] + st["warp_coalesced"] >= int(off[-1])
+        assert_cache_invariants(c)
