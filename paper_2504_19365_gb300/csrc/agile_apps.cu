@@ -164,7 +164,7 @@ struct EmbApp {
     Cursor pf;  // prefetch cursor, `ahead` rows in front of the summation
     cur_init(a, pf);
     if (async && !issue_rows(d, a, pf, ahead)) return;
-    constexpr int RB = MF4 >= 8 ? 1 : 8 / MF4;
+    constexpr int RB = MF4 >= 8 ? 1 : 8 / MF4;  // rows of an all-resident bag loaded before the next probe
     Prep cur;
     prep(d, a.warp, cur);
     for (uint32_t b = a.warp; b < n_bags; b += a.n_warps) {

@@ -214,9 +214,9 @@ __device__ __forceinline__ void set_error(const Dev &d, int code) {
 }
 __device__ __forceinline__ bool aborted(const Dev &d) { return ld_rlx32(&d.run->error) != 0; }
 
-__device__ __forceinline__ void backoff(uint32_t &ns) {
+__device__ __forceinline__ void backoff(uint32_t &ns, uint32_t cap = 2048) {
   __nanosleep(ns);
-  ns = ns < 2048 ? ns * 2 : 2048;
+  ns = ns < cap ? ns * 2 : cap;
 }
 
 // ---------------------------------------------------------------- cache geometry
@@ -656,9 +656,10 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
           ok = false;
         } else {
           // wait for the in-flight line without holding anything, then re-probe
+          // (short sleeps: a fill completes within microseconds)
           uint64_t t = ld_acq64(&d.tag[line]);
-          if (tag_page(t) == page && tag_state(t) == ST_BUSY) backoff(ns);
-          else if (!issued) backoff(ns);
+          if (tag_page(t) == page && tag_state(t) == ST_BUSY) backoff(ns, 512);
+          else if (!issued) backoff(ns, 512);
         }
       }
     }
@@ -921,7 +922,16 @@ static __device__ uint32_t emu_serve(const Dev &d, uint32_t q) {
   uint32_t *es = &d.emu[q * 4];
   uint32_t f = 0, k = 0;
   uint64_t now = gtimer();
-  if (l == 0) {
+  if (l == 0 && d.lat_ns == 0 && d.ns_per_page == 0) {
+    // no latency model: every command the doorbell exposes is due at once.  The fetch
+    // counter is read before the doorbell, so with f still current (checked by the
+    // compare-and-swap) the doorbell is at most depth-1 commands ahead of it and
+    // (db - f) mod depth is the exact number of unfetched commands.
+    f = ld_acq32(&es[0]);
+    uint32_t db = ld_acq32(&d.sq_db[q]);
+    k = min((db - (f & d.dmask)) & d.dmask, kEmuBatch);
+    if (k && atomicCAS(&es[0], f, f + k) != f) k = 0;
+  } else if (l == 0) {
     // `seen` must be read before the doorbell: it only ever takes doorbell values read
     // earlier, so seen <= tail here and (db - seen) mod depth is the exact number of
     // newly exposed commands (never a wrapped-around difference)
@@ -960,6 +970,7 @@ static __device__ uint32_t emu_serve(const Dev &d, uint32_t q) {
   k = __shfl_sync(kFull, k, 0);
   if (!k) return 0;
   f = __shfl_sync(kFull, f, 0);
+  __syncwarp();  // lane 0's acquire of the doorbell orders the SQE reads of every lane
   // command fields: lane i < k reads SQE f+i
   uint32_t dw0 = 0, nlb = 0, status = 0;
   uint64_t prp1 = 0, slba = 0;
@@ -1060,24 +1071,30 @@ static __device__ void service_loop(const Dev &d, uint32_t n_app, uint64_t deadl
     // device engine: serve one queue per iteration, the first one with work found from
     // a start that rotates over the queues and differs between engines, so that every
     // queue is visited often and commands do not wait behind long scans
+    // (the doorbells and fetch counters of four windows of 32 queues are read in one
+    // round trip; they only select a queue, emu_serve checks them again)
     uint32_t r = (uint32_t)(((uint64_t)iter * nsw + sw) % d.Q);
-    for (uint32_t w = 0; w < windows; ++w) {
-      uint32_t off = w * 32 + l;
-      uint32_t q = (r + off) % d.Q;
-      bool has = false;
-      if (off < d.Q) {
-        uint32_t *es = &d.emu[q * 4];
-        uint32_t db = ld_acq32(&d.sq_db[q]);
-        uint32_t f = ld_rlx32(&es[0]);
-        has = ((db - (f & d.dmask)) & d.dmask) != 0;
+    uint32_t qsel = ~0u;
+    for (uint32_t w0 = 0; w0 < windows && qsel == ~0u; w0 += 4) {
+      uint32_t dbv[4], fv[4];
+#pragma unroll
+      for (uint32_t j = 0; j < 4; ++j) {
+        uint32_t off = (w0 + j) * 32 + l;
+        dbv[j] = fv[j] = 0;
+        if (off < d.Q) {
+          uint32_t q = (r + off) % d.Q;
+          dbv[j] = ld_rlx32(&d.sq_db[q]);
+          fv[j] = ld_rlx32(&d.emu[q * 4]);
+        }
       }
-      unsigned m = __ballot_sync(kFull, has);
-      if (m) {
-        uint32_t qj = __shfl_sync(kFull, q, __ffs(m) - 1);
-        if (emu_serve(d, qj)) progress = true;
-        break;
+#pragma unroll
+      for (uint32_t j = 0; j < 4; ++j) {
+        uint32_t off = (w0 + j) * 32 + l;
+        unsigned m = __ballot_sync(kFull, off < d.Q && ((dbv[j] - (fv[j] & d.dmask)) & d.dmask) != 0);
+        if (m && qsel == ~0u) qsel = (r + (w0 + j) * 32 + (uint32_t)(__ffs(m) - 1)) % d.Q;
       }
     }
+    if (qsel != ~0u && emu_serve(d, qsel)) progress = true;
     // completion side (Alg. 1) for the queues this warp polls
     for (uint32_t q = sw; q < d.Q; q += nsw) progress |= cq_poll(d, q);
     if (progress) {
