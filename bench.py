@@ -236,6 +236,17 @@ def measure_link_peak(torch, dev):
     return best
 
 
+def reduce_over_ranks(torch, ms, work, world, device="cpu"):
+    """Whole-job figures of a weak-scaling replica run: each timed region takes the
+    slowest rank's time (MAX), units of work add up over the ranks (SUM)."""
+    vals = torch.tensor(ms, dtype=torch.float64, device=device)
+    wk = torch.tensor(work, dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(wk, op=torch.distributed.ReduceOp.SUM)
+    return vals.tolist(), wk.tolist()
+
+
 def run_bfs(args, torch, ag, dev, rank, world):
     t_setup = time.perf_counter()
     n, off, cols = synth.rmat_csr(3, 20, 16)
@@ -315,13 +326,8 @@ def run_bfs(args, torch, ag, dev, rank, world):
     if err:
         raise RuntimeError(f"device error: {ag.strerror(err)}")
 
-    vals = torch.tensor([ms_async, ms_sync, ms_e2e], dtype=torch.float64, device=dev)
-    wk = torch.tensor([work_async, work_sync, work_e2e], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(wk, op=torch.distributed.ReduceOp.SUM)
-    ms_async, ms_sync, ms_e2e = vals.tolist()
-    work_async, work_sync, work_e2e = wk.tolist()
+    (ms_async, ms_sync, ms_e2e), (work_async, work_sync, work_e2e) = reduce_over_ranks(
+        torch, [ms_async, ms_sync, ms_e2e], [work_async, work_sync, work_e2e], world, dev)
     link_peak = measure_link_peak(torch, dev)
     launches = args.steps * len(srcs)
     t_launch = ms_async / launches * 1e-3
@@ -605,9 +611,21 @@ def run_hits(args, torch, ag, dev):
             algo = nb * pool * (dim * 4 + 8) + (nb + 1) * 8 + nb * dim * 4
             res[name] = {"lookups_per_s": nb * pool / t, "ms_per_launch": t * 1e3, "misses": st["misses"],
                          "roofline": {"bound": "hbm", "achieved": algo / t / 1e9, "peak": HBM_PEAK, "unit": "GB/s",
-                                      "frac": algo / t / 1e9 / HBM_PEAK, "algorithmic_bytes_per_launch": algo,
+                                      "frac": algo / t / 1e9 / HBM_PEAK,
+                                      "traffic": recorded_traffic("engine_kernel<EmbApp<1,3>>"),
+                                      "kernel": "engine_kernel<EmbApp<1,3>>", "algorithmic_bytes_per_launch": algo,
                                       "peak_source": "measured (MEASURED_PEAKS hbm_gbs, copy read+write)"}}
         res["error"] = ag.agile_check(ctx)
+        # context: the library embedding bag of torch over the same table held plainly in HBM
+        T = torch.empty((rows, dim), dtype=torch.float32, device=dev).normal_()
+        for _ in range(3):
+            torch.nn.functional.embedding_bag(idx, T, off[:-1], mode="sum")
+        ms = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            ms += timed(torch, lambda: torch.nn.functional.embedding_bag(idx, T, off[:-1], mode="sum"))
+        res["torch_embedding_bag_hbm_lookups_per_s"] = nb * pool / (ms / args.steps * 1e-3)
+        del T
         res["workload"] = "65,536 bags x 16 uniform lookups, 2,097,152 x 128 FP32 table (1 GiB) fully cached (all hits)"
     finally:
         ag.agile_destroy(ctx)
