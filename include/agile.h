@@ -222,13 +222,14 @@ AGILE_API int agile_bfs(agile_ctx *ctx, uint64_t offsets_byte0, uint64_t cols_by
  * call (code being captured into a CUDA graph, latency-critical loops where an
  * allocation's device synchronisation is not acceptable).  The paper has no
  * counterpart: it is an addition of this library.  agile_bfs allocates a queue of long
- * adjacency lists on first use; this entry point uses a fixed 1 MiB device array
- * compiled into the library instead and calls no cudaMalloc/cudaFree.
- * n_cols: number of int32 column entries of the graph; graphs with more than
- * 33,553,408 column entries (32,768 queue slots of 1,024 entries) are rejected with
- * AGILE_EINVAL and a message on stderr.  The first call on a device looks up the
- * array's device address (make that first call before any stream capture).  All calls
- * on a device share the array: calls of this entry point that overlap on one GPU race. */
+ * adjacency lists and a visited bitmap on first use; this entry point uses fixed device
+ * arrays compiled into the library instead (1 MiB and 4 MiB) and calls no
+ * cudaMalloc/cudaFree.  n_cols: number of int32 column entries of the graph; graphs
+ * with more than 33,553,408 column entries (32,768 queue slots of 1,024 entries) or
+ * more than 33,554,432 vertices are rejected with AGILE_EINVAL and a message on
+ * stderr.  The first call on a device looks up the arrays' device addresses (make that
+ * first call before any stream capture).  All calls on a device share the arrays:
+ * calls of this entry point that overlap on one GPU race. */
 AGILE_API int agile_bfs_noalloc(agile_ctx *ctx, uint64_t offsets_byte0, uint64_t cols_byte0,
                                 uint32_t n_vertices, uint64_t n_cols, int32_t src, int32_t *d_level,
                                 uint64_t *d_edges_scanned, uint32_t mode, void *stream);

@@ -332,11 +332,11 @@ struct PipeApp {
 //          issues all of its pages before it is scanned.
 // A warp keeps at most one line pinned between steps (the page it read last) and lets
 // it go before it requests or waits for any other page.
+// One slice (at most kSlice entries) of a long adjacency list, queued for any warp.
 struct HubEntry {
-  long long s, e;
-  unsigned int next;  // next slice to hand out
-  unsigned int pad;
-  unsigned long long ready;  // (call epoch << 32) | (level + 1), written after s, e, next
+  long long p0, p1;          // column entries [p0, p1)
+  unsigned long long ready;  // (call epoch << 32) | (level + 1), written after p0, p1
+  unsigned long long pad;
 };
 
 // Every BFS call gets a fresh epoch, so an entry left by an earlier call or level can
@@ -352,6 +352,7 @@ struct BfsApp {
   HubEntry *hubq;
   uint32_t hub_cap;
   uint64_t epoch;
+  uint32_t *vis;  // visited bitmap: bit u set once level[u] is set (read through L1, may lag)
 
   static constexpr uint32_t kChunk = 128;
 
@@ -373,24 +374,46 @@ struct BfsApp {
     }
   }
 
-  // Element at byte `byte` of the array at store page `page0`, for lanes with `want`,
-  // through the cache: the warp walks the distinct pages of the requests.
-  template <typename T>
-  __device__ bool gather(const Dev &d, const AppCtx &a, uint64_t page0, bool want, uint64_t byte, T &val,
-                         Pin &pc) const {
-    uint64_t pg = page0 + byte / kPage;
-    uint32_t in = (uint32_t)(byte % kPage);
-    bool todo = want;
+  // Elements at bytes byte[0..N) of the array at store page `page0`, for the lanes'
+  // elements with `want`, through the cache: the warp walks the distinct pages of the
+  // requests, one pinned page at a time; the loads of all elements on the pinned page
+  // are issued together.
+  template <typename T, int N>
+  __device__ bool gather_n(const Dev &d, const AppCtx &a, uint64_t page0, const bool (&want)[N],
+                           const uint64_t (&byte)[N], T (&val)[N], Pin &pc) const {
+    uint64_t pg[N];
+    uint32_t in[N];
+    bool todo[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      pg[i] = page0 + byte[i] / kPage;
+      in[i] = (uint32_t)(byte[i] % kPage);
+      todo[i] = want[i];
+    }
     for (;;) {
-      if (pc.valid && todo && pg == pc.page) {
-        const uint8_t *src = line_ptr(d, pc.line) + in;
-        if (sizeof(T) == 8) val = (T)ld_cg_s64(src);
-        else val = (T)ld_cg_s32(src);
-        todo = false;
+      if (pc.valid) {
+        const uint8_t *base = line_ptr(d, pc.line);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          if (todo[i] && pg[i] == pc.page) {
+            if (sizeof(T) == 8) val[i] = (T)ld_cg_s64(base + in[i]);
+            else val[i] = (T)ld_cg_s32(base + in[i]);
+            todo[i] = false;
+          }
+        }
       }
-      unsigned m = __ballot_sync(kFull, todo);
+      bool any = false;
+      uint64_t nxt = 0;
+#pragma unroll
+      for (int i = N - 1; i >= 0; --i) {
+        if (todo[i]) {
+          any = true;
+          nxt = pg[i];
+        }
+      }
+      unsigned m = __ballot_sync(kFull, any);
       if (!m) return true;
-      uint64_t p = __shfl_sync(kFull, pg, __ffs(m) - 1);
+      uint64_t p = __shfl_sync(kFull, nxt, __ffs(m) - 1);
       release(d, pc);
       uint32_t line;
       if (!warp_pin_page(d, p, a.q0, a.deadline, line)) return false;
@@ -400,27 +423,80 @@ struct BfsApp {
     }
   }
 
-  __device__ __forceinline__ void visit(bool act, int32_t u, int32_t L, uint32_t &found) const {
-    if (act && (uint32_t)u < n) {
-      if (ld_rlx32((const uint32_t *)&level[u]) == 0xFFFFFFFFu && atomicCAS((int *)&level[u], -1, L + 1) == -1)
+  // Neighbours u[i] of the lanes (where act[i]): a set bit of the visited bitmap skips
+  // u (the bitmap is read through L1 and may lag, since bits only go from 0 to 1: a
+  // clear bit is confirmed against level[u]); the compare-and-swap of level[u] from -1
+  // to L+1 discovers u, and its winner sets the bit.
+  template <int N>
+  __device__ __forceinline__ void visit_n(const bool (&act)[N], const int32_t (&u)[N], int32_t L,
+                                          uint32_t &found) const {
+    uint32_t w[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) w[i] = (act[i] && (uint32_t)u[i] < n) ? __ldca(&vis[(uint32_t)u[i] >> 5]) : ~0u;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      uint32_t b = 1u << ((uint32_t)u[i] & 31);
+      if (!(w[i] & b) && ld_rlx32((const uint32_t *)&level[u[i]]) == 0xFFFFFFFFu &&
+          atomicCAS((int *)&level[u[i]], -1, L + 1) == -1) {
         found++;
+        atomicOr(&vis[(uint32_t)u[i] >> 5], b);
+      }
     }
   }
 
-  // queue a list of at least kHub entries for slicing; false if this lane keeps it
+  // both offsets of each lane's vertex (lanes with f): start s and end e of its list
+  __device__ bool read_offsets(const Dev &d, const AppCtx &a, uint32_t v, bool f, int64_t &s, int64_t &e,
+                               Pin &pc) const {
+    bool want[2] = {f, f};
+    uint64_t byte[2] = {(uint64_t)v * 8, (uint64_t)v * 8 + 8};
+    int64_t val[2] = {0, 0};
+    if (!gather_n<int64_t, 2>(d, a, off_page0, want, byte, val, pc)) return false;
+    s = val[0];
+    e = val[1];
+    return true;
+  }
+
+  // Queue the lanes' lists of at least kHub entries as slices of at most kSlice entries:
+  // one atomic add reserves consecutive record indices for all of the warp's slices,
+  // then the warp writes the records, each published by its ready word.  A level has at
+  // most (column entries) / kHub slices, which the queue holds; should a reservation
+  // still run past the queue's end, its records inside the queue are published empty
+  // and the lanes scan their lists here.  False for a lane that keeps its list.
   __device__ bool push_hub(const Dev &d, uint32_t deg, int64_t s, int64_t e, int32_t L) const {
+    unsigned l = lane_id();
     bool hub = deg >= kHub;
-    if (__any_sync(kFull, hub) && hub) {
-      uint32_t idx = atomicAdd(&d.run->hub_count[L & 1], 1u);
-      if (idx < hub_cap) {
-        HubEntry *h = &hubq[idx];
-        h->s = s;
-        h->e = e;
-        h->next = 0;
-        __threadfence();
-        st_rel64(&h->ready, tag(L));
-      } else {
-        hub = false;  // queue full: scanned here
+    unsigned hm = __ballot_sync(kFull, hub);
+    if (!hm) return false;
+    uint32_t sl = hub ? (deg + kSlice - 1) / kSlice : 0;
+    uint32_t incl = sl;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(kFull, incl, o);
+      if (l >= (unsigned)o) incl += t;
+    }
+    uint32_t excl = incl - sl;
+    uint32_t tot = __shfl_sync(kFull, incl, 31);
+    uint32_t base = 0;
+    if (l == 0) base = atomicAdd(&d.run->hub_count[L & 1], tot);
+    base = __shfl_sync(kFull, base, 0);
+    const uint64_t t = tag(L);
+    if ((uint64_t)base + tot > hub_cap) {
+      for (uint64_t j = (uint64_t)base + l; j < hub_cap; j += 32) {
+        hubq[j].p0 = hubq[j].p1 = 0;
+        st_rel64(&hubq[j].ready, t);
+      }
+      return false;  // scanned here
+    }
+    for (unsigned m = hm; m; m &= m - 1) {
+      int h = __ffs(m) - 1;
+      int64_t sh = __shfl_sync(kFull, s, h), eh = __shfl_sync(kFull, e, h);
+      uint32_t bh = base + __shfl_sync(kFull, excl, h), nh = __shfl_sync(kFull, sl, h);
+      for (uint32_t j = l; j < nh; j += 32) {
+        HubEntry *r = &hubq[bh + j];
+        int64_t p0 = sh + (int64_t)j * kSlice;
+        r->p0 = p0;
+        r->p1 = min(eh, p0 + (int64_t)kSlice);
+        st_rel64(&r->ready, t);
       }
     }
     return hub;
@@ -438,23 +514,29 @@ struct BfsApp {
     }
     uint32_t excl = incl - dg;
     uint32_t total = __shfl_sync(kFull, incl, 31);
-    for (uint32_t k0 = 0; k0 < total; k0 += 32) {
-      uint32_t k = k0 + l;
-      bool act = k < total;
-      // owner lane j: the last lane whose exclusive prefix is <= k
-      uint32_t j = 0;
+    // two 32-entry steps at a time: their loads are in flight together
+    for (uint32_t k0 = 0; k0 < total; k0 += 64) {
+      bool act[2];
+      uint64_t byte[2];
+      int32_t u[2] = {0, 0};
 #pragma unroll
-      for (int step = 16; step >= 1; step >>= 1) {
-        uint32_t cand = j + step;
-        uint32_t ex = __shfl_sync(kFull, excl, cand & 31);
-        if (cand < 32 && ex <= k) j = cand;
+      for (int h = 0; h < 2; ++h) {
+        uint32_t k = k0 + 32 * h + l;
+        act[h] = k < total;
+        // owner lane j: the last lane whose exclusive prefix is <= k
+        uint32_t j = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          uint32_t cand = j + step;
+          uint32_t ex = __shfl_sync(kFull, excl, cand & 31);
+          if (cand < 32 && ex <= k) j = cand;
+        }
+        int64_t sj = __shfl_sync(kFull, s, j);
+        uint32_t exj = __shfl_sync(kFull, excl, j);
+        byte[h] = ((uint64_t)sj + (k - exj)) * 4;
       }
-      int64_t sj = __shfl_sync(kFull, s, j);
-      uint32_t exj = __shfl_sync(kFull, excl, j);
-      uint64_t pos = (uint64_t)sj + (k - exj);
-      int32_t u = 0;
-      if (!gather<int32_t>(d, a, col_page0, act, pos * 4, u, pc)) return false;
-      visit(act, u, L, found);
+      if (!gather_n<int32_t, 2>(d, a, col_page0, act, byte, u, pc)) return false;
+      visit_n<2>(act, u, L, found);
     }
     return true;
   }
@@ -466,8 +548,7 @@ struct BfsApp {
     bool f = v < n && ld_rlx32((const uint32_t *)&level[v]) == (uint32_t)L;
     if (!__any_sync(kFull, f)) return true;
     int64_t s = 0, e = 0;
-    if (!gather<int64_t>(d, a, off_page0, f, (uint64_t)v * 8, s, pc)) return false;
-    if (!gather<int64_t>(d, a, off_page0, f, (uint64_t)v * 8 + 8, e, pc)) return false;
+    if (!read_offsets(d, a, v, f, s, e, pc)) return false;
     uint32_t deg = f ? (uint32_t)(e - s) : 0;
     scanned += __reduce_add_sync(kFull, deg);
     bool hub = push_hub(d, deg, s, e, L);
@@ -512,8 +593,7 @@ struct BfsApp {
     uint32_t v = v0 + lane_id();
     int64_t e = 0;
     s = 0;
-    if (!gather<int64_t>(d, a, off_page0, f, (uint64_t)v * 8, s, pc)) return false;
-    if (!gather<int64_t>(d, a, off_page0, f, (uint64_t)v * 8 + 8, e, pc)) return false;
+    if (!read_offsets(d, a, v, f, s, e, pc)) return false;
     uint32_t deg = f ? (uint32_t)(e - s) : 0;
     scanned += __reduce_add_sync(kFull, deg);
     bool hub = push_hub(d, deg, s, e, L);
@@ -558,78 +638,69 @@ struct BfsApp {
     }
   }
 
-  // Take slices of the queued long lists of level L until none is left.  A warp looks
-  // at 32 queued lists at once (one per lane, from a shared cursor), claims a slice of
-  // one that still has slices (different warps pick different lists), and moves the
-  // cursor past the leading lists that are used up, so the cost per warp grows with
-  // the number of lists / 32, not with the number of lists.  Lists queued after this
-  // warp leaves are sliced by the warps that queued them, which run this same loop.
+  // Take queued slices of level L, one ticket (a record index) at a time, until every
+  // slice is taken.  A ticket waits, holding no pin, for its record to be published;
+  // it is past the last slice when every warp has finished its own vertices (no more
+  // reservations come) and the reserved count is at most the ticket.  Each warp so ends
+  // with one ticket past the last slice.  Waiting warps watch their own record and look
+  // at the shared counters only now and then.
   __device__ bool help_hubs(const Dev &d, const AppCtx &a, int32_t L, uint32_t &found, Pin &pc) const {
     unsigned l = lane_id();
-    uint32_t ns = 64;
     const uint64_t want_tag = tag(L);
+    const int par = L & 1;
     for (;;) {
-      uint32_t c = 0, cur = 0;
-      if (l == 0) {
-        c = min(ld_acq32(&d.run->hub_count[L & 1]), hub_cap);
-        cur = ld_acq32(&d.run->hub_cursor[L & 1]);
-      }
-      c = __shfl_sync(kFull, c, 0);
-      cur = __shfl_sync(kFull, cur, 0);
-      if (cur >= c) return true;
-      uint32_t i = cur + l;
-      bool in = i < c, ready = false, left = false;
-      int64_t s = 0, e = 0;
-      uint32_t slices = 0;
-      if (in) {
-        HubEntry *h = &hubq[i];
-        ready = ld_acq64(&h->ready) == want_tag;
-        if (ready) {
-          s = ld_cg_s64(&h->s);
-          e = ld_cg_s64(&h->e);
-          slices = (uint32_t)((e - s + kSlice - 1) / kSlice);
-          left = ld_rlx32(&h->next) < slices;
+      uint32_t k = 0;
+      if (l == 0) k = atomicAdd(&d.run->hub_cursor[par], 1u);
+      k = __shfl_sync(kFull, k, 0);
+      if (k >= hub_cap) return true;
+      HubEntry *r = &hubq[k];
+      uint32_t ns = 64;
+      int state = 0;  // 1: record published, 2: past the last slice
+      for (uint32_t spin = 0;; ++spin) {
+        if (l == 0) {
+          if (ld_acq64(&r->ready) == want_tag) {
+            state = 1;
+          } else if ((spin & 7) == 7 && ld_acq32(&d.run->units_done[par]) >= a.n_warps &&
+                     ld_acq32(&d.run->hub_count[par]) <= k) {
+            state = 2;
+          }
         }
-      }
-      unsigned m = __ballot_sync(kFull, left);
-      unsigned used = __ballot_sync(kFull, !in || (ready && !left));
-      // leading lists that are used up: move the shared cursor past them
-      uint32_t lead = (used == kFull) ? 32u : (uint32_t)(__ffs(~used) - 1);
-      if (lead && l == 0) atomicMax(&d.run->hub_cursor[L & 1], min(cur + lead, c));
-      if (!m) {
-        if (lead) continue;
+        state = __shfl_sync(kFull, state, 0);
+        if (state) break;
+        release(d, pc);
         if (gtimer() > a.deadline || aborted(d)) {
           if (l == 0) set_error(d, -110);
           return false;
         }
-        backoff(ns);  // queued lists not yet published
-        continue;
+        backoff(ns, 1024);
       }
-      // pick one of the lists with slices left; spread warps over them
-      uint32_t nth = a.warp % __popc(m);
-      unsigned mm = m;
-      for (uint32_t t = 0; t < nth; ++t) mm &= mm - 1;
-      int j = __ffs(mm) - 1;
-      uint32_t k = 0;
-      if (l == (unsigned)j) k = atomicAdd(&hubq[i].next, 1u);
-      k = __shfl_sync(kFull, k, j);
-      s = __shfl_sync(kFull, s, j);
-      e = __shfl_sync(kFull, e, j);
-      slices = __shfl_sync(kFull, slices, j);
-      if (k >= slices) continue;  // lost the race for its last slice
-      ns = 64;
-      int64_t p0 = s + (int64_t)k * kSlice, p1 = min(e, p0 + (int64_t)kSlice);
+      if (state == 2) return true;
+      int64_t p0 = 0, p1 = 0;
+      if (l == 0) {
+        p0 = ld_cg_s64(&r->p0);
+        p1 = ld_cg_s64(&r->p1);
+      }
+      p0 = __shfl_sync(kFull, p0, 0);
+      p1 = __shfl_sync(kFull, p1, 0);
+      if (p1 <= p0) continue;  // an empty record (a reservation past the queue's end)
       if (mode == AGILE_ASYNC) {
         uint64_t q0p = col_page0 + ((uint64_t)p0 * 4) / kPage, q1p = col_page0 + ((uint64_t)(p1 - 1) * 4) / kPage;
         uint64_t pg = q0p + l;
         bool want = pg <= q1p && !(pc.valid && pc.page == pg);
         if (__any_sync(kFull, want) && !warp_request(d, want, pg, a.q0, false, a.deadline)) return false;
       }
-      for (int64_t pos = p0 + l; pos - l < p1; pos += 32) {
-        bool on = pos < p1;
-        int32_t u = 0;
-        if (!gather<int32_t>(d, a, col_page0, on, (uint64_t)(on ? pos : p0) * 4, u, pc)) return false;
-        visit(on, u, L, found);
+      for (int64_t b0 = p0; b0 < p1; b0 += 64) {
+        bool on[2];
+        uint64_t byte[2];
+        int32_t u[2] = {0, 0};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          int64_t pos = b0 + 32 * h + l;
+          on[h] = pos < p1;
+          byte[h] = (uint64_t)(on[h] ? pos : p0) * 4;
+        }
+        if (!gather_n<int32_t, 2>(d, a, col_page0, on, byte, u, pc)) return false;
+        visit_n<2>(on, u, L, found);
       }
     }
   }
@@ -646,6 +717,7 @@ struct BfsApp {
         st_rlx32(&d.run->work[(L + 1) & 1], 0u);
         st_rlx32(&d.run->hub_count[(L + 1) & 1], 0u);
         st_rlx32(&d.run->hub_cursor[(L + 1) & 1], 0u);
+        st_rlx32(&d.run->units_done[(L + 1) & 1], 0u);
         st_rlx64(&d.run->acc[1 + (L + 1) % 3], 0ull);
       }
       uint32_t found = 0;
@@ -663,6 +735,12 @@ struct BfsApp {
           if (!ok) break;
         }
       }
+      // this warp queues no more slices of level L
+      __syncwarp();
+      if (l == 0) {
+        fence_ar();
+        atomicAdd(&d.run->units_done[L & 1], 1u);
+      }
       if (ok) help_hubs(d, a, L, found, pc);
       release(d, pc);
       uint32_t tot = __reduce_add_sync(kFull, found);
@@ -678,9 +756,10 @@ struct BfsApp {
   }
 };
 
-__global__ void bfs_init_kernel(int32_t *level, uint32_t n, int32_t src) {
+__global__ void bfs_init_kernel(int32_t *level, uint32_t *vis, uint32_t n, int32_t src) {
   uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (i < n) level[i] = (i == (uint64_t)src) ? 0 : -1;
+  if (i < (n + 31ull) / 32) vis[i] = (i == (uint64_t)src / 32) ? 1u << (src % 32) : 0u;
 }
 
 // rows a warp pins together: with `warps` warps each holding that many lines at once,
@@ -702,14 +781,14 @@ int bfs_check(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_
 
 int bfs_launch(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_t n_vertices, int32_t src,
                int32_t *d_level, uint64_t *d_edges_scanned, uint32_t mode, void *stream, HubEntry *hubq,
-               uint32_t hub_cap) {
+               uint32_t hub_cap, uint32_t *vis) {
   cudaStream_t s = as_stream(stream);
-  bfs_init_kernel<<<(n_vertices + 255) / 256, 256, 0, s>>>(d_level, n_vertices, src);
+  bfs_init_kernel<<<(n_vertices + 255) / 256, 256, 0, s>>>(d_level, vis, n_vertices, src);
   AGILE_CUDA_TRY(cudaGetLastError());
   if (d_edges_scanned) AGILE_CUDA_TRY(cudaMemsetAsync(d_edges_scanned, 0, 8, s));
   BfsApp app{offsets_byte0 / kPage, cols_byte0 / kPage, n_vertices, d_level,
              (unsigned long long *)d_edges_scanned, mode, hubq, hub_cap,
-             g_bfs_epoch.fetch_add(1) & 0xFFFFFFFFull};
+             g_bfs_epoch.fetch_add(1) & 0xFFFFFFFFull, vis};
   // sync: about two lines per warp (one pinned, one being filled); async: four, since a
   // warp also holds the pages it requested for its next units
   return launch_engine(c, app, stream, warps_for_cache(c, mode == AGILE_ASYNC ? 4 : 2, 32));
@@ -721,32 +800,38 @@ int bfs_launch(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32
 // latency-critical loops in which an allocation's implicit device synchronisation
 // would stall every other stream.  For them agile_bfs_noalloc keeps the long-list
 // queue, the only scratch the BFS kernel needs beyond the context, in this fixed
-// device array.  Every GPU that loads the library holds it (1 MiB) until the process
-// exits.  Host code must not pass the array's name to a kernel: on the host it is a
+// device array, and the visited bitmap in a second one.  Every GPU that loads the
+// library holds them (1 MiB + 4 MiB) until the process exits.  Host code must not pass the array's name to a kernel: on the host it is a
 // stand-in symbol, not a device address, so its address is fetched once per device with
 // cudaGetSymbolAddress, with that device current, on the first call on that device.
-// No field needs clearing between calls: an entry is written before it is published,
-// and publication carries the call's epoch, so what an earlier call left behind is never
-// taken for a live entry.  All calls on one device share the array, so calls of this
+// No queue entry needs clearing between calls: an entry is written before it is
+// published, and publication carries the call's epoch, so what an earlier call left
+// behind is never taken for a live entry; the bitmap is cleared by every call.  All calls on one device share the array, so calls of this
 // entry point that overlap on that GPU (from any context or stream) race on it.
 constexpr uint32_t kNoAllocHubMax = 32768;
+constexpr uint32_t kNoAllocVisWords = 1u << 20;  // vertices up to 2^25
 static __device__ __align__(256) HubEntry g_bfs_hub_scratch[kNoAllocHubMax];
+static __device__ __align__(256) uint32_t g_bfs_vis_scratch[kNoAllocVisWords];
 
-int noalloc_scratch(int device, HubEntry **out) {
+int noalloc_scratch(int device, HubEntry **out, uint32_t **vis_out) {
   static std::mutex mu;
   static HubEntry *ptr[128] = {};
+  static uint32_t *vptr[128] = {};
   if (device < 0 || device >= 128) return AGILE_ENODEV;
   std::lock_guard<std::mutex> g(mu);
   if (!ptr[device]) {
-    void *p = nullptr;
+    void *p = nullptr, *q = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_bfs_hub_scratch);
-    if (e != cudaSuccess || !p) {
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&q, g_bfs_vis_scratch);
+    if (e != cudaSuccess || !p || !q) {
       fprintf(stderr, "agile: cudaGetSymbolAddress of the BFS scratch failed: %s\n", cudaGetErrorString(e));
       return AGILE_ECUDA;
     }
     ptr[device] = (HubEntry *)p;
+    vptr[device] = (uint32_t *)q;
   }
   *out = ptr[device];
+  *vis_out = vptr[device];
   return AGILE_OK;
 }
 
@@ -830,8 +915,15 @@ int agile_bfs(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_
     AGILE_CUDA_TRY(cudaMalloc(&c->bfs_hubq, cap * sizeof(HubEntry)));
     c->bfs_hub_cap = (uint32_t)cap;
   }
+  uint64_t words = ((uint64_t)n_vertices + 31) / 32;
+  if (!c->bfs_vis || c->bfs_vis_words < words) {
+    if (c->bfs_vis) cudaFree(c->bfs_vis);
+    c->bfs_vis = nullptr;
+    AGILE_CUDA_TRY(cudaMalloc(&c->bfs_vis, words * 4));
+    c->bfs_vis_words = words;
+  }
   return bfs_launch(c, offsets_byte0, cols_byte0, n_vertices, src, d_level, d_edges_scanned, mode, stream,
-                    (HubEntry *)c->bfs_hubq, c->bfs_hub_cap);
+                    (HubEntry *)c->bfs_hubq, c->bfs_hub_cap, (uint32_t *)c->bfs_vis);
 }
 
 int agile_bfs_noalloc(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_t n_vertices,
@@ -848,12 +940,18 @@ int agile_bfs_noalloc(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0,
             (unsigned long long)(kNoAllocHubMax - 1) * BfsApp::kHub);
     return AGILE_EINVAL;
   }
+  if (((uint64_t)n_vertices + 31) / 32 > kNoAllocVisWords) {
+    fprintf(stderr, "agile_bfs_noalloc: %u vertices; this entry point has a visited bitmap for up to %llu; "
+            "use agile_bfs\n", n_vertices, (unsigned long long)kNoAllocVisWords * 32);
+    return AGILE_EINVAL;
+  }
   AGILE_CUDA_TRY(cudaSetDevice(c->device));
   HubEntry *scratch = nullptr;
-  r = noalloc_scratch(c->device, &scratch);
+  uint32_t *vis = nullptr;
+  r = noalloc_scratch(c->device, &scratch, &vis);
   if (r) return r;
   return bfs_launch(c, offsets_byte0, cols_byte0, n_vertices, src, d_level, d_edges_scanned, mode, stream,
-                    scratch, kNoAllocHubMax);
+                    scratch, kNoAllocHubMax, vis);
 }
 
 }  // extern "C"

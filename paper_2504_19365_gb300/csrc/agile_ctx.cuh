@@ -20,6 +20,8 @@ struct agile_ctx {
   int last_cuda_error = 0;
   void *bfs_hubq = nullptr;  // BFS scratch: queue of long adjacency lists
   uint32_t bfs_hub_cap = 0;
+  void *bfs_vis = nullptr;  // BFS scratch: visited bitmap
+  uint64_t bfs_vis_words = 0;
   void *train_scratch = nullptr;  // backward scratch: sorted keys, bag of each position
   size_t train_scratch_bytes = 0;
 };

@@ -70,8 +70,10 @@ struct RunState {
   uint32_t work[4];       // dynamic work counters
   unsigned long long acc[4];  // accumulators (edges scanned, discovered vertices, ...)
   uint32_t flag[4];
-  uint32_t hub_count[2];   // BFS: long adjacency lists queued for slicing, per level parity
-  uint32_t hub_cursor[2];  // BFS: first queued list that may still have slices
+  // BFS slice queue, per level parity, each on a line of its own (hot words)
+  alignas(128) uint32_t hub_count[2];  // slices of long adjacency lists reserved
+  alignas(128) uint32_t hub_cursor[2];  // next slice ticket
+  alignas(128) uint32_t units_done[2];  // warps that finished their own vertices
 };
 
 struct Dev {

@@ -522,6 +522,7 @@ int agile_destroy(agile_ctx *c) {
   }
   for (void *p : c->dallocs) cudaFree(p);
   if (c->bfs_hubq) cudaFree(c->bfs_hubq);
+  if (c->bfs_vis) cudaFree(c->bfs_vis);
   if (c->train_scratch) cudaFree(c->train_scratch);
   if (c->store_host) cudaFreeHost(c->store_host);
   delete c;

@@ -66,3 +66,15 @@ def test_noalloc_bfs_rejects_graph_beyond_its_scratch():
         with pytest.raises(ag.AgileError) as e:
             ag.agile_bfs_noalloc(c.h, 0, col0, n, too_many, 0, lv.data_ptr(), 0, ag.AGILE_SYNC, c.stream)
         assert e.value.code == ag.AGILE_EINVAL
+
+
+def test_noalloc_bfs_rejects_more_vertices_than_its_bitmap():
+    # 2^25 + 1 vertices need one bitmap word more than the fixed array has; the call is
+    # rejected on the host before anything is launched
+    nv = (1 << 25) + 1
+    store = ((nv + 1) * 8 + 4095) // 4096 * 4096 + 4096
+    with Ctx(store, cache_bytes=64 * 4096, ways=8, num_queues=8, queue_depth=64) as c:
+        lv = torch.empty(1, dtype=torch.int32, device=DEV)
+        with pytest.raises(ag.AgileError) as e:
+            ag.agile_bfs_noalloc(c.h, 0, store - 4096, nv, 1, 0, lv.data_ptr(), 0, ag.AGILE_SYNC, c.stream)
+        assert e.value.code == ag.AGILE_EINVAL
