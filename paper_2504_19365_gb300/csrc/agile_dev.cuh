@@ -1063,7 +1063,7 @@ static __device__ uint32_t emu_serve(const Dev &d, uint32_t q) {
 // q = cta, cta + grid, ...  The other warps run the application.  No kernel of the
 // library ever waits on another launch: the device, the pollers and the waiters are
 // co-resident warps of one grid, and every wait is bounded by a deadline.
-static __device__ void service_loop(const Dev &d, uint32_t n_app, uint64_t deadline) {
+static __device__ void service_loop(const Dev &d, uint32_t n_app, uint64_t deadline, bool poll) {
   uint32_t sw = blockIdx.x, nsw = gridDim.x;
   unsigned l = lane_id();
   uint32_t ns = 32;
@@ -1098,7 +1098,8 @@ static __device__ void service_loop(const Dev &d, uint32_t n_app, uint64_t deadl
     }
     if (qsel != ~0u && emu_serve(d, qsel)) progress = true;
     // completion side (Alg. 1) for the queues this warp polls
-    for (uint32_t q = sw; q < d.Q; q += nsw) progress |= cq_poll(d, q);
+    if (poll)
+      for (uint32_t q = sw; q < d.Q; q += nsw) progress |= cq_poll(d, q);
     if (progress) {
       ns = 32;
       continue;
@@ -1112,6 +1113,34 @@ static __device__ void service_loop(const Dev &d, uint32_t n_app, uint64_t deadl
         if ((ld_acq64(&d.sq_resv[q]) >> 32) != 0) drained = false;
       if (__all_sync(kFull, drained)) break;
     }
+    if (gtimer() > deadline) {
+      if (l == 0) set_error(d, -110);
+      break;
+    }
+    __nanosleep(ns);
+    ns = ns < 256 ? ns * 2 : 256;
+  }
+}
+
+// A dedicated Alg. 1 poller of queue q: an application warp that sits out the call.
+// Ends when every application warp is done and the queue has nothing in flight.
+static __device__ void poller_loop(const Dev &d, uint32_t q, uint32_t n_app, uint64_t deadline) {
+  unsigned l = lane_id();
+  uint32_t ns = 32;
+  for (;;) {
+    if (cq_poll(d, q)) {
+      ns = 32;
+      continue;
+    }
+    uint32_t done = 0;
+    uint64_t resv = 0;
+    if (l == 0) {
+      done = ld_acq32(&d.run->app_done);
+      resv = ld_acq64(&d.sq_resv[q]);
+    }
+    done = __shfl_sync(kFull, done, 0);
+    resv = __shfl_sync(kFull, resv, 0);
+    if (done >= n_app && (resv >> 32) == 0) break;
     if (gtimer() > deadline) {
       if (l == 0) set_error(d, -110);
       break;
@@ -1168,16 +1197,21 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<App>::value) engine_kernel
   uint32_t warp = threadIdx.x >> 5;
   uint32_t n_app = gridDim.x * (kWarps - 1);
   uint64_t deadline = gtimer() + (d.session_ns ? d.session_ns : d.timeout_ns);
+  uint32_t n_active = (d.app_active && d.app_active < n_app) ? d.app_active : n_app;
+  // when at least Q application warps sit out the call, the first Q of them poll one
+  // queue each, and the service warps only serve the device
+  const bool pollers = n_app - n_active >= d.Q;
   if (warp == 0) {
-    service_loop(d, n_app, deadline + d.timeout_ns);
+    service_loop(d, n_app, deadline + d.timeout_ns, !pollers);
     return;
   }
   AppCtx a;
   a.warp = blockIdx.x * (kWarps - 1) + (warp - 1);
-  a.n_warps = (d.app_active && d.app_active < n_app) ? d.app_active : n_app;
+  a.n_warps = n_active;
   if (a.warp >= a.n_warps) {
     // not needed by this call: keeps the working set of the active warps in the cache
     if (lane_id() == 0) atomicAdd(&d.run->app_done, 1u);
+    if (pollers && a.warp - a.n_warps < d.Q) poller_loop(d, a.warp - a.n_warps, n_app, deadline + d.timeout_ns);
     return;
   }
   // home queue by thread index, spread so that the lanes of a warp and the lane 0 of
