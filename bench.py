@@ -470,7 +470,7 @@ def run_dlrm(args, torch, ag, dev):
             go(ag.AGILE_SYNC, 0, cold=False)
             w0 = go(ag.AGILE_SYNC, 0, cold=False)
             w1 = go(ag.AGILE_SYNC, 2000, cold=False)
-            per_iter = max(1e-9, (w1 - w0) / 2000)
+            per_iter = max(1e-6, (w1 - w0) / 2000)
             pts = []
             for r in (0.25, 0.5, 1, 2, 4, 8):
                 iters = max(1, int(r * t_io / per_iter))
@@ -491,6 +491,85 @@ def run_dlrm(args, torch, ag, dev):
         if ctx is not None:
             ag.agile_destroy(ctx)
     return res
+
+
+def run_sweeps(args, torch, ag, dev):
+    """Sensitivity of sync vs async (the sweeps of the paper's Sec. 4.4 DLRM study) on the
+    lookup + compute pipeline at a compute-to-I/O ratio of 1: batch size (bags per
+    batch, 1-2048), queue pairs (1-16 at depth 64) and cache size (1 MiB-2 GiB).  Tables:
+    8 x 1,000,000 x 64 FP32 (2.05 GB) on the store, Zipf 1.05 rows, pooling 32; default
+    cache 256 MiB, 128 queues x 256.  Each point is timed at 32 application warps (one
+    block of 1,024 threads, as in the paper's overlap experiment) and at the full grid,
+    each call from a cold cache."""
+    nt, rows, dim, pool = 8, 1_000_000, 64, 32
+    stride = round_page(rows * dim * 4)
+    stream = torch.cuda.current_stream().cuda_stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    zipf = synth.Zipf(rows, 1.05, permute=True, seed=4)
+
+    def context(cache_bytes=256 << 20, queues=128, depth=256):
+        cfg = ag.agile_config_default(store_bytes=stride * nt, cache_bytes=cache_bytes, ways=8, num_queues=queues,
+                                      queue_depth=depth, device=torch.cuda.current_device(),
+                                      wait_timeout_ns=60_000_000_000)
+        ctx = ag.agile_init(cfg)
+        fill_tables(ag, ctx, nt, rows, dim, stride)
+        return ctx
+
+    def point(ctx, nbags, batches):
+        idx = zipf.rows(5, batches * nt * nbags * pool).reshape(batches, nt, nbags, pool)
+        d_idx = torch.from_numpy(idx).to(dev)
+        out = torch.empty((batches, nbags, nt * dim), dtype=torch.float32, device=dev)
+        res = {}
+        for appw, name in ((32, "warps_32"), (0, "full_grid")):
+            ag.agile_config_parallelism(ctx, appw)
+
+            def go(mode, iters, cold=True):
+                if cold:
+                    ag.agile_invalidate(ctx, stream)
+                flush.zero_()
+                return timed(torch, lambda: ag.agile_embedding_pipeline(
+                    ctx, 0, stride, nt, rows, dim, d_idx.data_ptr(), pool, nbags, batches, iters, out.data_ptr(),
+                    mode, stream))
+            go(ag.AGILE_SYNC, 0)
+            t_io = go(ag.AGILE_SYNC, 0)
+            w0 = go(ag.AGILE_SYNC, 0, cold=False)
+            w1 = go(ag.AGILE_SYNC, 20000, cold=False)
+            # one round is a few dependent FMAs per element: at least 1 ns, whatever the
+            # calibration noise
+            per_iter = max(1e-6, (w1 - w0) / 20000)
+            iters = max(1, int(t_io / per_iter))
+            ts = go(ag.AGILE_SYNC, iters)
+            ta = go(ag.AGILE_ASYNC, iters)
+            res[name] = {"sync_ms": round(ts, 3), "async_ms": round(ta, 3), "async_speedup": round(ts / ta, 3),
+                         "iters": iters}
+        ag.agile_config_parallelism(ctx, 0)
+        err = ag.agile_check(ctx)
+        if err:
+            raise RuntimeError(f"device error: {ag.strerror(err)}")
+        return res
+
+    out = {"workload": "8 x 1,000,000 x 64 FP32 tables (2.05 GB), Zipf 1.05, pooling 32, compute at CTC 1, "
+                       "cold cache per call"}
+    ctx = context()
+    try:
+        out["batch_size"] = {str(nb): point(ctx, nb, max(1, min(16, 2048 // nb))) for nb in (1, 16, 128, 1024, 2048)}
+    finally:
+        ag.agile_destroy(ctx)
+    out["queue_pairs_depth_64"] = {}
+    for q in (1, 2, 4, 8, 16):
+        ctx = context(queues=q, depth=64)
+        try:
+            out["queue_pairs_depth_64"][str(q)] = point(ctx, 2048, 1)
+        finally:
+            ag.agile_destroy(ctx)
+    out["cache_bytes"] = {}
+    for cb in (1 << 20, 16 << 20, 256 << 20, 2 << 30):
+        ctx = context(cache_bytes=cb)
+        try:
+            out["cache_bytes"][f"{cb >> 20}MiB"] = point(ctx, 2048, 1)
+        finally:
+            ag.agile_destroy(ctx)
+    return out
 
 
 def run_serving(torch, ag, dev, ctx, nt, rows, dim, stride, stream, n_req=600):
@@ -638,7 +717,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bfs", choices=["bfs", "embedding", "hits"])
+    ap.add_argument("--workload", default="bfs", choices=["bfs", "embedding", "hits", "sweeps"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--wait-timeout-s", type=float, default=10.0,
@@ -673,6 +752,9 @@ def main():
             res["train"] = run_train(args, torch, ag, dev)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline_bfs(*graph)
+    elif args.workload == "sweeps":
+        res = {"metric": "async over sync speedup of the lookup + compute pipeline (sensitivity sweeps)",
+               "unit": "x", "n_gpus": world, "data": "synthetic", "sweeps": run_sweeps(args, torch, ag, dev)}
     elif args.workload == "hits":
         h = run_hits(args, torch, ag, dev)
         res = {"metric": "embedding-bag lookups/s, all cache hits (sync)", "value": h["sync"]["lookups_per_s"],
