@@ -154,7 +154,7 @@ AGILE_API int agile_read_async(agile_ctx *ctx, const uint64_t *d_pages, uint32_t
 AGILE_API int agile_write_async(agile_ctx *ctx, const uint64_t *d_pages, uint32_t n,
                       const void *d_src, agile_token *d_tok, void *stream);
 
-/* wait (Sec. 3.2.1 "lock a"): d_status[i] = 0 when token i completed cleanly,
+/* wait (Sec. 3.2.1, the per-request transaction barrier): d_status[i] = 0 when token i completed cleanly,
  * AGILE_EIO when it completed with an error, AGILE_ETIMEDOUT when it is still
  * outstanding after cfg->wait_timeout_ns. */
 AGILE_API int agile_wait(agile_ctx *ctx, const agile_token *d_tok, uint32_t n, int32_t *d_status,
@@ -201,8 +201,10 @@ AGILE_API int agile_embedding_bag_backward(agile_ctx *ctx, uint64_t table_byte0,
  * numbers.  For every (batch t, bag b): out[t][b][k*dim + d] = sum over p of
  * T_k[idx[t][k][b][p]][d] in increasing p (FP32), then compute_iters rounds of
  * x = fma(x, 1 - 2^-12, 2^-10) per element.  d_out: float [n_batches][n_bags][n_tables*dim].
- * AGILE_SYNC requests each row when summed; AGILE_ASYNC requests a warp's next unit
- * of work before gathering and computing the current one. */
+ * AGILE_SYNC requests each row when summed; AGILE_ASYNC keeps the pages of a warp's
+ * upcoming rows requested ahead of its gather and compute: as many rows as the cache
+ * holds for the warps running (half of its lines), at most one unit (n_tables *
+ * pooling rows) ahead. */
 AGILE_API int agile_embedding_pipeline(agile_ctx *ctx, uint64_t table_byte0, uint64_t table_stride,
                                        uint32_t n_tables, uint32_t rows, uint32_t dim,
                                        const int64_t *d_idx, uint32_t pooling, uint32_t n_bags,

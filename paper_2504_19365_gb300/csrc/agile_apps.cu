@@ -219,15 +219,17 @@ struct EmbApp {
 };
 
 // ============================================================================ lookup + compute pipeline
-// The DLRM-shaped overlap experiment (Sec. 4.2 computation-to-communication ratio,
-// Sec. 4.4 "AGILE async prefetches the next epoch while computing this one").
+// The DLRM-shaped overlap experiment (Sec. 4.2 computation-to-communication ratio;
+// Sec. 4.4: in async mode the data of the next epoch is fetched during this one's compute).
 // Work unit = (batch t, bag b): sum-pool `pooling` rows of each of n_tables tables
 // into out[t][b][k*dim ...], then the compute phase: every output element goes through
 // `iters` fused multiply-adds x = fma(x, kFmaA, kFmaB).  Warp w takes units w, w+W, ...
 // in batch-major order.
 //   SYNC : rows are requested when summed (a miss stalls the warp), then compute.
-//   ASYNC: before gathering unit u the warp requests every page of its next unit u+W,
-//          so that fetch overlaps the gather and the compute of unit u.
+//   ASYNC: the warp keeps the pages of its next `ahead` rows requested (its units u,
+//          u+W, ... as one row stream), so that fetch overlaps the gather and the
+//          compute in front of them; `ahead` is what half of the cache holds for the
+//          warps running, at most one unit.
 // The compute is a phase of the same launch (not a separate kernel): the emulated
 // device only runs while a library launch is resident.
 constexpr float kFmaA = 0.999755859375f;  // 1 - 2^-12
@@ -243,17 +245,26 @@ struct PipeApp {
   float *out;         // [batches][bags][tables*dim]
   uint32_t mode;
   uint32_t group;     // rows pinned together at most (cache-sized), 1..32
+  uint32_t ahead;     // async: rows of the warp's row stream requested ahead (cache-sized)
 
   __device__ __forceinline__ uint64_t row_page(uint32_t k, uint64_t r) const {
     return page0 + ((uint64_t)k * tstride + r * dim * 4) / kPage;
   }
 
-  __device__ bool prefetch_unit(const Dev &d, const AppCtx &a, uint64_t u) const {
-    uint64_t t = u / n_bags, b = u % n_bags;
-    uint32_t per = n_tables * pooling;
-    for (uint32_t base = 0; base < per; base += 32) {
-      uint32_t q = base + lane_id();
-      bool want = q < per;
+  // Position in the warp's row stream: its units u, u + W, ..., the rows of a unit in
+  // table-major order.
+  struct Cursor {
+    uint64_t u;
+    uint32_t q;
+  };
+  // request the pages of the next `cnt` rows of the stream from cursor c (advances c)
+  __device__ bool issue_ahead(const Dev &d, const AppCtx &a, Cursor &c, uint32_t cnt, uint64_t units) const {
+    const uint32_t per = n_tables * pooling;
+    while (cnt && c.u < units) {
+      uint32_t take = min(cnt, min(32u, per - c.q));
+      uint32_t q = c.q + lane_id();
+      bool want = lane_id() < take;
+      uint64_t t = c.u / n_bags, b = c.u % n_bags;
       uint32_t k = want ? q / pooling : 0, p = want ? q % pooling : 0;
       uint64_t r = want ? (uint64_t)idx[((t * n_tables + k) * n_bags + b) * pooling + p] : 0;
       if (want && r >= rows) {
@@ -261,6 +272,12 @@ struct PipeApp {
         want = false;
       }
       if (!warp_request(d, want, row_page(k, r), a.q0, false, a.deadline)) return false;
+      c.q += take;
+      cnt -= take;
+      if (c.q == per) {
+        c.q = 0;
+        c.u += a.n_warps;
+      }
     }
     return true;
   }
@@ -270,9 +287,11 @@ struct PipeApp {
     const uint32_t nf4 = dim / 4;
     const bool async = mode == AGILE_ASYNC;
     const uint64_t units = (uint64_t)n_batches * n_bags;
-    if (async && a.warp < units && !prefetch_unit(d, a, a.warp)) return;
+    // async: the pages of the next `ahead` rows of the stream are requested before the
+    // rows in front of them are gathered and computed on
+    Cursor pf{a.warp, 0};
+    if (async && !issue_ahead(d, a, pf, ahead, units)) return;
     for (uint64_t u = a.warp; u < units; u += a.n_warps) {
-      if (async && u + a.n_warps < units && !prefetch_unit(d, a, u + a.n_warps)) return;
       uint64_t t = u / n_bags, b = u % n_bags;
       float *o = out + u * (uint64_t)n_tables * dim;
       for (uint32_t k = 0; k < n_tables; ++k) {
@@ -290,6 +309,7 @@ struct PipeApp {
           uint64_t byte = (uint64_t)k * tstride + r * dim * 4;
           for (uint32_t g0 = 0; g0 < cnt; g0 += group) {
             uint32_t g1 = min(cnt, g0 + group);
+            if (async && !issue_ahead(d, a, pf, g1 - g0, units)) return;
             if (!gather_sum<MF4>(d, a, g0, g1, page0 + byte / kPage, (uint32_t)(byte % kPage), nf4, acc)) return;
           }
         }
@@ -885,19 +905,22 @@ int agile_embedding_pipeline(agile_ctx *c, uint64_t table_byte0, uint64_t table_
     return AGILE_EINVAL;
   if (((uintptr_t)d_out) & 15) return AGILE_EINVAL;
   uint64_t units = (uint64_t)n_batches * n_bags;
-  uint32_t per_unit = n_tables * pooling;  // pages a warp holds or requests ahead
-  // async: a warp also holds the pages it requested for its next unit; about half of a
-  // unit's rows are taken to need a line of their own
-  uint32_t warps = (uint32_t)std::min<uint64_t>(
-      units, warps_for_cache(c, mode == AGILE_ASYNC ? std::max<uint32_t>(4, per_unit / 2) : 4, 32));
-  if (dim <= 128) {
-    PipeApp<1> app{table_byte0 / kPage, table_stride, n_tables, rows, dim, d_idx, pooling, n_bags, n_batches,
-                   compute_iters, d_out, mode, pin_group(c, running_app_warps<PipeApp<1>>(c, warps))};
+  uint32_t per_unit = n_tables * pooling;
+  // a warp per unit while the rows each warp pins or requests ahead fit in the cache:
+  // half of the lines for pin groups, half for the rows requested ahead (async), at
+  // most one unit ahead
+  uint32_t warps = (uint32_t)std::min<uint64_t>(units, warps_for_cache(c, 4, 32));
+  auto go = [&](auto tag) {
+    using App = decltype(tag);
+    uint32_t run = running_app_warps<App>(c, warps);
+    uint64_t ahead = mode == AGILE_ASYNC ? c->dev.nlines / (2ull * run) * c->cfg.prefetch_depth : 0;
+    ahead = std::max<uint64_t>(1, std::min<uint64_t>(per_unit, ahead));
+    App app{table_byte0 / kPage, table_stride, n_tables, rows, dim, d_idx, pooling, n_bags, n_batches,
+            compute_iters, d_out, mode, pin_group(c, run), (uint32_t)ahead};
     return launch_engine(c, app, stream, warps);
-  }
-  PipeApp<kMaxF4> app{table_byte0 / kPage, table_stride, n_tables, rows, dim, d_idx, pooling, n_bags, n_batches,
-                      compute_iters, d_out, mode, pin_group(c, running_app_warps<PipeApp<kMaxF4>>(c, warps))};
-  return launch_engine(c, app, stream, warps);
+  };
+  if (dim <= 128) return go(PipeApp<1>{});
+  return go(PipeApp<kMaxF4>{});
 }
 
 int agile_bfs(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_t n_vertices, int32_t src,
