@@ -12,6 +12,7 @@ Functions and the passage each restates:
                                        Sec. 4.4
   embedding_bag / _backward / sgd   -- sum-pooled lookups of Sec. 4.4, fixed order
   bfs                               -- FIFO-queue BFS over CSR (Sec. 4.5)
+  spmv                              -- y = A x over CSR with FP32 values (Sec. 4.5)
   fma_chain / embedding_pipeline    -- compute phase of the overlap experiment (Sec. 4.2)
   ideal_speedup                     -- Eq. 1
   set_of                            -- the cache's set-index function
@@ -68,6 +69,8 @@ def lib():
         L.orc_sgd.argtypes = [vp, u64, u32, vp, vp, C.c_float]
         L.orc_bfs.argtypes = [u64, vp, vp, i32, vp]
         L.orc_bfs.restype = u64
+        L.orc_spmv.argtypes = [u64, vp, vp, vp, vp, vp]
+        L.orc_spmv.restype = u64
         L.orc_fma_chain.argtypes = [vp, u64, u32, C.c_float, C.c_float]
         L.orc_ideal_speedup.argtypes = [C.c_double]
         L.orc_ideal_speedup.restype = C.c_double
@@ -210,6 +213,19 @@ def bfs(offsets: np.ndarray, cols: np.ndarray, src: int):
     level = np.empty(max(n, 1), dtype=np.int32)
     scanned = int(lib().orc_bfs(n, _p(o), _p(c), int(src), _p(level)))
     return level[:n], scanned
+
+
+def spmv(offsets: np.ndarray, cols: np.ndarray, vals: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """y = A x, A in CSR (int64 offsets, int32 cols, float32 vals), FP32 in increasing
+    entry order per row."""
+    o = _c(offsets, np.int64)
+    c = _c(cols, np.int32)
+    v = _c(vals, np.float32)
+    xv = _c(x, np.float32)
+    n = o.size - 1
+    y = np.empty(max(n, 1), dtype=np.float32)
+    lib().orc_spmv(n, _p(o), _p(c), _p(v), _p(xv), _p(y))
+    return y[:n]
 
 
 FMA_A = 0.999755859375   # 1 - 2^-12

@@ -19,6 +19,10 @@
  *                           element, indices added in increasing order (Sec. 4.4 DLRM
  *                           lookups); backward scatter-add and an SGD step.
  *   - BFS                 : textbook FIFO-queue breadth-first search over CSR (Sec. 4.5).
+ *   - SpMV                : y = A x over the same CSR layout plus FP32 values (Sec. 4.5
+ *                           runs SpMV on the graphs of its BFS), one FP32 accumulator per
+ *                           row, entries added in increasing order, each product rounded
+ *                           before it is added.
  *   - compute phase       : the FP32 multiply-add chain that follows each lookup batch
  *                           in the overlap experiment (Sec. 4.2).
  *   - ideal speedup       : Eq. 1.
@@ -341,6 +345,23 @@ uint64_t orc_bfs(uint64_t n, const int64_t *offsets, const int32_t *cols, int32_
 /* ------------------------------------------------------------------ Eq. 1 */
 
 /* Ideal overlap speedup of Eq. 1: 1 + CTC for 0 <= CTC <= 1, else 1 + 1/CTC. */
+/* SpMV over CSR (Sec. 4.5): y[v] = sum over j in [offsets[v], offsets[v+1]) of
+ * vals[j] * x[cols[j]], the sum taken in increasing j in FP32 starting from +0, each
+ * product rounded to FP32 before it is added (no fused multiply-add).  Returns the
+ * number of entries (the CSR size). */
+uint64_t orc_spmv(uint64_t n, const int64_t *offsets, const int32_t *cols, const float *vals, const float *x,
+                  float *y) {
+  for (uint64_t v = 0; v < n; ++v) {
+    float acc = 0.0f;
+    for (int64_t j = offsets[v]; j < offsets[v + 1]; ++j) {
+      float prod = vals[j] * x[cols[j]];
+      acc = acc + prod;
+    }
+    y[v] = acc;
+  }
+  return n ? (uint64_t)offsets[n] : 0;
+}
+
 double orc_ideal_speedup(double ctc) {
   if (ctc < 0) return 0.0 / 0.0;
   return ctc <= 1.0 ? 1.0 + ctc : 1.0 + 1.0 / ctc;
