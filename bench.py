@@ -367,6 +367,58 @@ def run_bfs(args, torch, ag, dev, rank, world):
     return result, (off, cols, srcs)
 
 
+def run_spmv(args, torch, ag, dev, off, cols):
+    """SpMV through the cache (Sec. 4.5): the RMAT scale-20 graph with N(0,1) FP32 values
+    (seed 6) and x (seed 7); cache 1/8 of the column and value arrays.  A step is one
+    y = A x from an invalidated cache with L2 flushed (both untimed).  Metric: matrix
+    entries per second.  Host-link algorithmic bytes: 4 B column + 4 B value per entry
+    and 8 B offset per row."""
+    n = off.size - 1
+    vals = synth.normal(6, cols.size).astype(np.float32)
+    x = synth.normal(7, n).astype(np.float32)
+    col0 = round_page(off.nbytes)
+    val0 = col0 + round_page(cols.nbytes)
+    total = val0 + round_page(vals.nbytes)
+    cache = round_page((cols.nbytes + vals.nbytes) // 8) // (8 * 4096) * (8 * 4096)
+    cfg = ag.agile_config_default(store_bytes=total, cache_bytes=cache, ways=8, device=torch.cuda.current_device(),
+                                  wait_timeout_ns=int(args.wait_timeout_s * 1e9))
+    ctx = ag.agile_init(cfg)
+    stream = torch.cuda.current_stream().cuda_stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    try:
+        ag.agile_store_write(ctx, 0, off.ctypes.data, off.nbytes)
+        ag.agile_store_write(ctx, col0, cols.ctypes.data, cols.nbytes)
+        ag.agile_store_write(ctx, val0, vals.ctypes.data, vals.nbytes)
+        d_x = torch.from_numpy(x).to(dev)
+        d_y = torch.empty(n, dtype=torch.float32, device=dev)
+        ent = torch.zeros(1, dtype=torch.int64, device=dev)
+        res = {"workload": "RMAT scale 20 (1,048,576 rows, 31,402,030 entries) with N(0,1) FP32 values, "
+                           "cache 1/8 of the column and value arrays", "cache_bytes": cache}
+        for mode, name in ((ag.AGILE_ASYNC, "async"), (ag.AGILE_SYNC, "sync")):
+            ms = 0.0
+            for i in range(max(3, args.warmup) + args.steps):
+                ag.agile_invalidate(ctx, stream)
+                flush.zero_()
+                t = timed(torch, lambda: ag.agile_spmv(ctx, 0, col0, val0, n, n, d_x.data_ptr(), d_y.data_ptr(),
+                                                       ent.data_ptr(), mode, stream))
+                if i >= max(3, args.warmup):
+                    ms += t
+            t_call = ms / args.steps * 1e-3
+            algo = 8.0 * cols.size + 8.0 * (n + 1)
+            st = ag.agile_stats(ctx)
+            res[name] = {"entries_per_s": cols.size / t_call, "ms_per_call": t_call * 1e3,
+                         "roofline": {"bound": "host_link", "achieved": algo / t_call / 1e9,
+                                      "algorithmic_bytes_per_launch": algo}}
+        err = ag.agile_check(ctx)
+        if err:
+            raise RuntimeError(f"device error: {ag.strerror(err)}")
+        if int(ent.item()) != cols.size:
+            raise RuntimeError("entry count mismatch")
+    finally:
+        ag.agile_destroy(ctx)
+    return res
+
+
 def run_embedding(args, torch, ag, dev, rank, world):
     rows, dim, nb, pool, batches = 65536, 128, 256, 16, 16
     T = synth.table_normal(1, rows, dim)
@@ -746,6 +798,12 @@ def main():
     if args.workload == "bfs":
         res, graph = run_bfs(args, torch, ag, dev, rank, world)
         if not args.no_extras:
+            res["spmv"] = run_spmv(args, torch, ag, dev, graph[0], graph[1])
+            peak = res["roofline"]["peak"]
+            for m in ("async", "sync"):
+                rl = res["spmv"][m]["roofline"]
+                rl.update(peak=peak, unit="GB/s", frac=rl["achieved"] / peak,
+                          peak_source=res["roofline"]["peak_source"])
             res["embedding_bag"] = run_embedding(args, torch, ag, dev, rank, world)
             res["embedding_bag_hits"] = run_hits(args, torch, ag, dev)
             res["dlrm"] = run_dlrm(args, torch, ag, dev)

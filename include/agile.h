@@ -220,6 +220,24 @@ AGILE_API int agile_bfs(agile_ctx *ctx, uint64_t offsets_byte0, uint64_t cols_by
               uint32_t n_vertices, int32_t src, int32_t *d_level,
               uint64_t *d_edges_scanned, uint32_t mode, void *stream);
 
+/* Sparse matrix-vector product over a CSR matrix on the store (Sec. 4.5 runs SpMV
+ * over the CSR graphs of its BFS): int64 offsets [n_rows+1] at byte offsets_byte0,
+ * int32 column numbers at byte cols_byte0 and FP32 values at byte vals_byte0 (all
+ * three multiples of 4096; entry j of the matrix is cols[j], vals[j]), read through
+ * the cache.  d_x: float [n_cols] and d_y: float [n_rows], device memory of the
+ * caller (16-byte alignment not required).  d_y[v] = sum over j in
+ * [offsets[v], offsets[v+1]) of vals[j] * x[cols[j]] in FP32, each product rounded
+ * before it is added.  A row of fewer than 1024 entries is summed in increasing j
+ * (equal bit for bit to that order); a longer row is summed in slices of 2048 entries,
+ * each in increasing j, whose sums are added in the order they finish.  A column
+ * number >= n_cols contributes 0 and records AGILE_EINVAL (agile_check).
+ * *d_entries (uint64, device, may be NULL) = number of entries (offsets[n_rows] -
+ * offsets[0]).  mode as above.  Uses the library's slice-queue scratch (shared with
+ * agile_bfs; allocated on first use). */
+AGILE_API int agile_spmv(agile_ctx *ctx, uint64_t offsets_byte0, uint64_t cols_byte0, uint64_t vals_byte0,
+                         uint32_t n_rows, uint32_t n_cols, const float *d_x, float *d_y,
+                         uint64_t *d_entries, uint32_t mode, void *stream);
+
 /* BFS exactly as agile_bfs, for callers that cannot allocate device memory during the
  * call (code being captured into a CUDA graph, latency-critical loops where an
  * allocation's device synchronisation is not acceptable).  The paper has no

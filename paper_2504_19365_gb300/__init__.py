@@ -36,7 +36,7 @@ EXPORTED = [
     "agile_store_read", "agile_read_async", "agile_write_async", "agile_wait",
     "agile_prefetch", "agile_flush", "agile_invalidate", "agile_embedding_bag",
     "agile_embedding_bag_backward", "agile_embedding_pipeline", "agile_bfs",
-    "agile_bfs_noalloc", "agile_serve_start", "agile_serve_submit", "agile_serve_poll",
+    "agile_bfs_noalloc", "agile_spmv", "agile_serve_start", "agile_serve_submit", "agile_serve_poll",
     "agile_serve_stop", "agile_serve_replay",
     "agile_cache_replay", "agile_cache_tags", "agile_cache_lines", "agile_cache_sets",
     "agile_stats", "agile_reset_stats", "agile_check", "agile_launch_shape", "agile_strerror",
@@ -127,6 +127,7 @@ def lib():
                                                    vp]),
             "agile_bfs": (C.c_int, [vp, u64, u64, u32, i32, vp, vp, u32, vp]),
             "agile_bfs_noalloc": (C.c_int, [vp, u64, u64, u32, u64, i32, vp, vp, u32, vp]),
+            "agile_spmv": (C.c_int, [vp, u64, u64, u64, u32, u32, vp, vp, vp, u32, vp]),
             "agile_cache_replay": (C.c_int, [vp, vp, u32, vp, vp]),
             "agile_cache_tags": (C.c_int, [vp, vp]),
             "agile_cache_lines": (u64, [vp]),
@@ -238,6 +239,12 @@ def agile_embedding_pipeline(ctx, table_byte0, table_stride, n_tables, rows, dim
 def agile_bfs(ctx, offsets_byte0, cols_byte0, n_vertices, src, d_level, d_edges, mode, stream) -> int:
     return _ok(lib().agile_bfs(ctx, offsets_byte0, cols_byte0, n_vertices, src, d_level, d_edges, mode,
                                stream), "agile_bfs")
+
+
+def agile_spmv(ctx, offsets_byte0, cols_byte0, vals_byte0, n_rows, n_cols, d_x, d_y, d_entries, mode,
+               stream) -> int:
+    return _ok(lib().agile_spmv(ctx, offsets_byte0, cols_byte0, vals_byte0, n_rows, n_cols, d_x, d_y, d_entries,
+                                mode, stream), "agile_spmv")
 
 
 def agile_bfs_noalloc(ctx, offsets_byte0, cols_byte0, n_vertices, n_cols, src, d_level, d_edges, mode,

@@ -776,6 +776,418 @@ struct BfsApp {
   }
 };
 
+// ============================================================================ SpMV
+// y = A x over a CSR matrix on the store (Sec. 4.5 runs SpMV over the CSR graphs of its
+// BFS): int64 offsets, int32 columns and FP32 values are read through the cache; x and
+// y are device arrays of the caller.  Warps take chunks of kChunk consecutive rows, in
+// units of 32 rows (a lane owns a row); a unit's entries are flattened over the warp,
+// 32 a step, the column and the value of an entry each read through the cache.  The
+// offsets, column and value arrays each keep one pinned page; before a warp waits for a
+// page it lets the other two go, so it never waits while holding a pin.  A row's
+// products are added in increasing entry order: within a step by a chain over the
+// lanes (lane t adds its product to lane t-1's running sum), across steps through the
+// owner lane's running sum, so a row of fewer than kHub entries equals the sequential
+// definition bit for bit.  A row of at least kHub entries is queued as slices of
+// kSlice entries (the BFS slice queue); each slice is summed in order and added to y[v]
+// with an atomic add (y[v] = +0 is written before the slices are published), so such a
+// row is exact up to the order in which its slice sums arrive.
+//   SYNC : every page when needed.
+//   ASYNC: while the warp computes unit i, the offsets of unit i+1 are read and the
+//          column and value pages of its entries are requested, and the offsets pages
+//          of unit i+2 are requested.
+struct SpmvApp {
+  uint64_t off_page0, col_page0, val_page0;
+  uint32_t n;    // rows
+  const float *x;
+  uint32_t n_x;  // columns (length of x)
+  float *y;
+  unsigned long long *entries_out;
+  uint32_t mode;
+  HubEntry *hubq;
+  uint32_t hub_cap;
+  uint64_t epoch;
+
+  static constexpr uint32_t kChunk = 128;
+  static constexpr uint32_t kHub = 1024;
+  static constexpr uint32_t kSlice = 2048;
+
+  struct Pin {
+    uint64_t page;
+    uint32_t line;
+    bool valid;
+  };
+
+  __device__ __forceinline__ void release(const Dev &d, Pin &pc) const {
+    if (pc.valid) {
+      __syncwarp();
+      if (lane_id() == 0) cache_unpin(d, pc.line);
+      pc.valid = false;
+    }
+  }
+
+  // Elements at bytes byte[0..N) of the array at store page `page0`, for the elements
+  // with `want`, through pin `pc`: the warp walks the distinct pages of the requests.
+  // A page that is not resident is waited for only after o1 and o2 have been let go.
+  template <typename T, int N>
+  __device__ bool gather(const Dev &d, const AppCtx &a, uint64_t page0, const bool (&want)[N],
+                         const uint64_t (&byte)[N], T (&val)[N], Pin &pc, Pin &o1, Pin &o2) const {
+    uint64_t pg[N];
+    uint32_t in[N];
+    bool todo[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      pg[i] = page0 + byte[i] / kPage;
+      in[i] = (uint32_t)(byte[i] % kPage);
+      todo[i] = want[i];
+    }
+    for (;;) {
+      if (pc.valid) {
+        const uint8_t *base = line_ptr(d, pc.line);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          if (todo[i] && pg[i] == pc.page) {
+            if (sizeof(T) == 8) {
+              long long raw = ld_cg_s64(base + in[i]);
+              memcpy(&val[i], &raw, 8);
+            } else {
+              int raw = ld_cg_s32(base + in[i]);
+              memcpy(&val[i], &raw, 4);
+            }
+            todo[i] = false;
+          }
+        }
+      }
+      bool any = false;
+      uint64_t nxt = 0;
+#pragma unroll
+      for (int i = N - 1; i >= 0; --i) {
+        if (todo[i]) {
+          any = true;
+          nxt = pg[i];
+        }
+      }
+      unsigned m = __ballot_sync(kFull, any);
+      if (!m) return true;
+      uint64_t p = __shfl_sync(kFull, nxt, __ffs(m) - 1);
+      release(d, pc);
+      uint32_t line = 0;
+      if (warp_probe_pin(d, p, line) != P_HIT) {
+        release(d, o1);
+        release(d, o2);
+        if (!warp_pin_page(d, p, a.q0, a.deadline, line)) return false;
+      }
+      pc.page = p;
+      pc.line = line;
+      pc.valid = true;
+    }
+  }
+
+  // product of the entry at `pos` (lanes with act): vals[pos] * x[cols[pos]], rounded
+  __device__ bool product(const Dev &d, const AppCtx &a, bool act, uint64_t pos, float &prod, Pin &po, Pin &pcol,
+                          Pin &pval) const {
+    const bool w[1] = {act};
+    const uint64_t b[1] = {pos * 4};
+    int32_t col[1] = {0};
+    float val[1] = {0.f};
+    if (!gather<int32_t, 1>(d, a, col_page0, w, b, col, pcol, pval, po)) return false;
+    if (!gather<float, 1>(d, a, val_page0, w, b, val, pval, pcol, po)) return false;
+    prod = 0.f;
+    if (act) {
+      float xv = 0.f;
+      if ((uint32_t)col[0] < n_x) xv = __ldg(&x[col[0]]);
+      else set_error(d, AGILE_EINVAL);
+      prod = __fmul_rn(val[0], xv);
+    }
+    return true;
+  }
+
+  // In-order running sums over one step: unless it starts a row segment (its `run`
+  // already set by the caller), lane t adds its product to lane t-1's running sum.
+  __device__ __forceinline__ float chain(float run, float prod, bool cont) const {
+    unsigned l = lane_id();
+#pragma unroll
+    for (int t = 1; t < 32; ++t) {
+      float prev = __shfl_sync(kFull, run, t - 1);
+      if ((int)l == t && cont) run = __fadd_rn(prev, prod);
+    }
+    return run;
+  }
+
+  // both offsets of each lane's row (lanes with f)
+  __device__ bool read_offsets(const Dev &d, const AppCtx &a, uint32_t v, bool f, int64_t &s, int64_t &e, Pin &po,
+                               Pin &pcol, Pin &pval) const {
+    const bool want[2] = {f, f};
+    const uint64_t byte[2] = {(uint64_t)v * 8, (uint64_t)v * 8 + 8};
+    int64_t val[2] = {0, 0};
+    if (!gather<int64_t, 2>(d, a, off_page0, want, byte, val, po, pcol, pval)) return false;
+    s = val[0];
+    e = val[1];
+    return true;
+  }
+
+  // queue the lanes' rows of at least kHub entries as slices (as the BFS does); a lane
+  // whose row is queued writes y[v] = +0 before its slices are published
+  __device__ bool push_hub(const Dev &d, uint32_t v, uint32_t deg, int64_t s, int64_t e) const {
+    unsigned l = lane_id();
+    bool hub = deg >= kHub;
+    unsigned hm = __ballot_sync(kFull, hub);
+    if (!hm) return false;
+    uint32_t sl = hub ? (deg + kSlice - 1) / kSlice : 0;
+    uint32_t incl = sl;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(kFull, incl, o);
+      if (l >= (unsigned)o) incl += t;
+    }
+    uint32_t excl = incl - sl;
+    uint32_t tot = __shfl_sync(kFull, incl, 31);
+    uint32_t base = 0;
+    if (l == 0) base = atomicAdd(&d.run->hub_count[0], tot);
+    base = __shfl_sync(kFull, base, 0);
+    const uint64_t t = (epoch << 32) | 1u;
+    if ((uint64_t)base + tot > hub_cap) {
+      for (uint64_t j = (uint64_t)base + l; j < hub_cap; j += 32) {
+        hubq[j].p0 = hubq[j].p1 = 0;
+        st_rel64(&hubq[j].ready, t);
+      }
+      return false;  // summed here
+    }
+    if (hub) y[v] = 0.0f;
+    __syncwarp();
+    for (unsigned m = hm; m; m &= m - 1) {
+      int h = __ffs(m) - 1;
+      int64_t sh = __shfl_sync(kFull, s, h), eh = __shfl_sync(kFull, e, h);
+      uint32_t vh = __shfl_sync(kFull, v, h);
+      uint32_t bh = base + __shfl_sync(kFull, excl, h), nh = __shfl_sync(kFull, sl, h);
+      for (uint32_t j = l; j < nh; j += 32) {
+        HubEntry *r = &hubq[bh + j];
+        int64_t p0 = sh + (int64_t)j * kSlice;
+        r->p0 = p0;
+        r->p1 = min(eh, p0 + (int64_t)kSlice);
+        r->pad = vh;
+        __threadfence();  // y[v] = 0 (written by another lane) before the record is seen
+        st_rel64(&r->ready, t);
+      }
+    }
+    return hub;
+  }
+
+  // The rows [v0, v0 + 32): lane l's row starts at entry s and has `dg` entries summed
+  // here (0 for a queued row): flattened over the warp, summed in order; y written for
+  // the lanes with `keep`.
+  __device__ bool compute_unit(const Dev &d, const AppCtx &a, uint32_t v0, int64_t s, uint32_t dg, bool keep,
+                               Pin &po, Pin &pcol, Pin &pval) const {
+    unsigned l = lane_id();
+    uint32_t incl = dg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(kFull, incl, o);
+      if (l >= (unsigned)o) incl += t;
+    }
+    uint32_t excl = incl - dg;
+    uint32_t total = __shfl_sync(kFull, incl, 31);
+    float acc = 0.0f;  // this lane's row: running sum
+    for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+      uint32_t k = k0 + l;
+      bool act = k < total;
+      // owner lane j: the last lane whose exclusive prefix is <= k
+      uint32_t j = 0;
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        uint32_t cand = j + step;
+        uint32_t ex = __shfl_sync(kFull, excl, cand & 31);
+        if (cand < 32 && ex <= k) j = cand;
+      }
+      int64_t sj = __shfl_sync(kFull, s, j);
+      uint32_t exj = __shfl_sync(kFull, excl, j);
+      float prod = 0.f;
+      if (!product(d, a, act, act ? (uint64_t)sj + (k - exj) : 0, prod, po, pcol, pval)) return false;
+      float carry = __shfl_sync(kFull, acc, j);
+      bool first = act && (k == exj || l == 0);  // the row's first entry in this step
+      float run = first ? __fadd_rn(k == exj ? 0.0f : carry, prod) : prod;
+      run = chain(run, prod, act && !first);
+      // the owner takes its row's running sum from the row's last lane in this step
+      uint32_t endk = excl + dg;
+      bool mine = dg > 0 && excl < k0 + 32 && endk > k0;
+      uint32_t last = mine ? min(endk, k0 + 32) - 1 - k0 : 0;
+      float got = __shfl_sync(kFull, run, last);
+      if (mine) acc = got;
+    }
+    if (keep) y[v0 + l] = acc;
+    return true;
+  }
+
+  __device__ bool next_unit(const Dev &d, uint32_t nchunks, uint32_t &chunk, uint32_t &sub, uint32_t &v0) const {
+    if (sub >= kChunk) {
+      uint32_t c = 0;
+      if (lane_id() == 0) c = atomicAdd(&d.run->work[0], 1u);
+      chunk = __shfl_sync(kFull, c, 0);
+      sub = 0;
+      if (chunk >= nchunks || aborted(d)) return false;
+    }
+    v0 = chunk * kChunk + sub;
+    sub += 32;
+    return v0 < n;
+  }
+
+  // stage A: request the offsets pages of a unit (its offsets [v0, min(v0+32, n)])
+  __device__ bool stage_a(const Dev &d, const AppCtx &a, uint32_t v0) const {
+    uint32_t vend = min(v0 + 32, n);
+    uint64_t pa = off_page0 + ((uint64_t)v0 * 8) / kPage, pb = off_page0 + ((uint64_t)vend * 8) / kPage;
+    bool want = (lane_id() == 0) || (lane_id() == 1 && pb != pa);
+    return warp_request(d, want, lane_id() == 0 ? pa : pb, a.q0, false, a.deadline);
+  }
+
+  // stage B: read the offsets, queue long rows, request the unit's column and value pages
+  __device__ bool stage_b(const Dev &d, const AppCtx &a, uint32_t v0, int64_t &s, uint32_t &dg, bool &keep,
+                          unsigned long long &entries, Pin &po, Pin &pcol, Pin &pval) const {
+    uint32_t v = v0 + lane_id();
+    bool f = v < n;
+    int64_t e = 0;
+    s = 0;
+    if (!read_offsets(d, a, v, f, s, e, po, pcol, pval)) return false;
+    uint32_t deg = f ? (uint32_t)(e - s) : 0;
+    entries += __reduce_add_sync(kFull, deg);
+    bool hub = push_hub(d, v, deg, s, e);
+    dg = hub ? 0 : deg;
+    keep = f && !hub;
+    // the entries summed here lie in one span (queued rows are holes in it): request
+    // the span's pages of both arrays, at most 32 of each
+    long long lo = dg ? s : LLONG_MAX, hi = dg ? s + dg : 0;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      lo = min(lo, __shfl_xor_sync(kFull, lo, o));
+      hi = max(hi, __shfl_xor_sync(kFull, hi, o));
+    }
+    if (hi <= lo) return true;
+    uint64_t c0 = ((uint64_t)lo * 4) / kPage, c1 = ((uint64_t)(hi - 1) * 4) / kPage;
+    bool want = c0 + lane_id() <= c1;
+    if (!warp_request(d, want, col_page0 + c0 + lane_id(), a.q0, false, a.deadline)) return false;
+    return warp_request(d, want, val_page0 + c0 + lane_id(), a.q0, false, a.deadline);
+  }
+
+  // take queued slices until every slice is taken (the BFS slice queue, one level)
+  __device__ bool help_hubs(const Dev &d, const AppCtx &a, Pin &po, Pin &pcol, Pin &pval) const {
+    unsigned l = lane_id();
+    const uint64_t want_tag = (epoch << 32) | 1u;
+    for (;;) {
+      uint32_t k = 0;
+      if (l == 0) k = atomicAdd(&d.run->hub_cursor[0], 1u);
+      k = __shfl_sync(kFull, k, 0);
+      if (k >= hub_cap) return true;
+      HubEntry *r = &hubq[k];
+      uint32_t ns = 64;
+      int state = 0;  // 1: record published, 2: past the last slice
+      for (uint32_t spin = 0;; ++spin) {
+        if (l == 0) {
+          if (ld_acq64(&r->ready) == want_tag) {
+            state = 1;
+          } else if ((spin & 7) == 7 && ld_acq32(&d.run->units_done[0]) >= a.n_warps &&
+                     ld_acq32(&d.run->hub_count[0]) <= k) {
+            state = 2;
+          }
+        }
+        state = __shfl_sync(kFull, state, 0);
+        if (state) break;
+        release(d, po);
+        release(d, pcol);
+        release(d, pval);
+        if (gtimer() > a.deadline || aborted(d)) {
+          if (l == 0) set_error(d, -110);
+          return false;
+        }
+        backoff(ns, 1024);
+      }
+      if (state == 2) return true;
+      int64_t p0 = 0, p1 = 0;
+      uint32_t row = 0;
+      if (l == 0) {
+        p0 = ld_cg_s64(&r->p0);
+        p1 = ld_cg_s64(&r->p1);
+        row = (uint32_t)ld_cg_s64(&r->pad);
+      }
+      p0 = __shfl_sync(kFull, p0, 0);
+      p1 = __shfl_sync(kFull, p1, 0);
+      row = __shfl_sync(kFull, row, 0);
+      if (p1 <= p0) continue;  // an empty record (a reservation past the queue's end)
+      release(d, po);
+      if (mode == AGILE_ASYNC) {
+        uint64_t c0 = ((uint64_t)p0 * 4) / kPage, c1 = ((uint64_t)(p1 - 1) * 4) / kPage;
+        bool want = c0 + l <= c1;
+        if (!warp_request(d, want, col_page0 + c0 + l, a.q0, false, a.deadline)) return false;
+        if (!warp_request(d, want, val_page0 + c0 + l, a.q0, false, a.deadline)) return false;
+      }
+      float sum = 0.0f;  // the slice's running sum (the same in every lane)
+      for (int64_t b0 = p0; b0 < p1; b0 += 32) {
+        int64_t pos = b0 + l;
+        bool act = pos < p1;
+        float prod = 0.f;
+        if (!product(d, a, act, act ? (uint64_t)pos : (uint64_t)p0, prod, po, pcol, pval)) return false;
+        float run = (l == 0) ? __fadd_rn(sum, prod) : prod;
+        run = chain(run, prod, act && l != 0);
+        sum = __shfl_sync(kFull, run, (int)min((int64_t)31, p1 - 1 - b0));
+      }
+      if (l == 0) atomicAdd(&y[row], sum);
+    }
+  }
+
+  __device__ void run(const Dev &d, const AppCtx &a) const {
+    unsigned l = lane_id();
+    const uint32_t nchunks = (n + kChunk - 1) / kChunk;
+    unsigned long long entries = 0;
+    Pin po{0, 0, false}, pcol{0, 0, false}, pval{0, 0, false};
+    bool ok = true;
+    uint32_t chunk = 0, sub = kChunk;
+    if (mode == AGILE_ASYNC) {
+      uint32_t u0 = 0, v1 = 0, v2 = 0;
+      int64_t s0 = 0, s1 = 0;
+      uint32_t dg0 = 0, dg1 = 0;
+      bool k0 = false, k1 = false;
+      bool have0 = false, have1 = next_unit(d, nchunks, chunk, sub, v1), have2 = false;
+      if (have1) ok = stage_a(d, a, v1);
+      while (ok && (have0 || have1)) {
+        have2 = have1 && next_unit(d, nchunks, chunk, sub, v2);
+        if (have2) ok = stage_a(d, a, v2);
+        if (ok && have1) ok = stage_b(d, a, v1, s1, dg1, k1, entries, po, pcol, pval);
+        if (ok && have0) ok = compute_unit(d, a, u0, s0, dg0, k0, po, pcol, pval);
+        have0 = have1;
+        u0 = v1;
+        s0 = s1;
+        dg0 = dg1;
+        k0 = k1;
+        have1 = have2;
+        v1 = v2;
+      }
+    } else {
+      uint32_t v0 = 0;
+      while (ok && next_unit(d, nchunks, chunk, sub, v0)) {
+        uint32_t v = v0 + l;
+        bool f = v < n;
+        int64_t s = 0, e = 0;
+        ok = read_offsets(d, a, v, f, s, e, po, pcol, pval);
+        if (!ok) break;
+        uint32_t deg = f ? (uint32_t)(e - s) : 0;
+        entries += __reduce_add_sync(kFull, deg);
+        bool hub = push_hub(d, v, deg, s, e);
+        ok = compute_unit(d, a, v0, s, hub ? 0 : deg, f && !hub, po, pcol, pval);
+      }
+    }
+    // this warp queues no more slices
+    __syncwarp();
+    if (l == 0) {
+      fence_ar();
+      atomicAdd(&d.run->units_done[0], 1u);
+    }
+    if (ok) help_hubs(d, a, po, pcol, pval);
+    release(d, po);
+    release(d, pcol);
+    release(d, pval);
+    if (l == 0 && entries) atomicAdd(&d.run->acc[0], entries);
+    if (!app_barrier(d, a.n_warps, a.deadline)) return;
+    if (a.warp == 0 && l == 0 && entries_out) *entries_out = ld_acq64(&d.run->acc[0]);
+  }
+};
+
 __global__ void bfs_init_kernel(int32_t *level, uint32_t *vis, uint32_t n, int32_t src) {
   uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (i < n) level[i] = (i == (uint64_t)src) ? 0 : -1;
@@ -855,6 +1267,22 @@ int noalloc_scratch(int device, HubEntry **out, uint32_t **vis_out) {
   return AGILE_OK;
 }
 
+// Slice queue of a CSR walk (BFS, SpMV): a level has at most (column entries) / kHub
+// slices, so the entries the store can hold beyond cols_byte0 bound it.
+int ensure_slice_queue(agile_ctx *c, uint64_t cols_byte0) {
+  uint64_t cap = (c->cfg.store_bytes - cols_byte0) / 4 / BfsApp::kHub + 1;
+  if (cap > (1u << 22)) cap = 1u << 22;
+  if (cap < 1024) cap = 1024;
+  if (!c->bfs_hubq || c->bfs_hub_cap < cap) {
+    if (c->bfs_hubq) cudaFree(c->bfs_hubq);
+    c->bfs_hubq = nullptr;
+    c->bfs_hub_cap = 0;
+    AGILE_CUDA_TRY(cudaMalloc(&c->bfs_hubq, cap * sizeof(HubEntry)));
+    c->bfs_hub_cap = (uint32_t)cap;
+  }
+  return AGILE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -928,16 +1356,8 @@ int agile_bfs(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_
   int r = bfs_check(c, offsets_byte0, cols_byte0, n_vertices, src, d_level, mode);
   if (r) return r;
   AGILE_CUDA_TRY(cudaSetDevice(c->device));
-  // queue of long lists: at most (column entries) / kHub of them per level
-  uint64_t cap = (c->cfg.store_bytes - cols_byte0) / 4 / BfsApp::kHub + 1;
-  if (cap > (1u << 22)) cap = 1u << 22;
-  if (cap < 1024) cap = 1024;
-  if (!c->bfs_hubq || c->bfs_hub_cap < cap) {
-    if (c->bfs_hubq) cudaFree(c->bfs_hubq);
-    c->bfs_hubq = nullptr;
-    AGILE_CUDA_TRY(cudaMalloc(&c->bfs_hubq, cap * sizeof(HubEntry)));
-    c->bfs_hub_cap = (uint32_t)cap;
-  }
+  r = ensure_slice_queue(c, cols_byte0);
+  if (r) return r;
   uint64_t words = ((uint64_t)n_vertices + 31) / 32;
   if (!c->bfs_vis || c->bfs_vis_words < words) {
     if (c->bfs_vis) cudaFree(c->bfs_vis);
@@ -975,6 +1395,25 @@ int agile_bfs_noalloc(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0,
   if (r) return r;
   return bfs_launch(c, offsets_byte0, cols_byte0, n_vertices, src, d_level, d_edges_scanned, mode, stream,
                     scratch, kNoAllocHubMax, vis);
+}
+
+int agile_spmv(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint64_t vals_byte0, uint32_t n_rows,
+               uint32_t n_cols, const float *d_x, float *d_y, uint64_t *d_entries, uint32_t mode, void *stream) {
+  if (!c || mode > 1) return AGILE_EINVAL;
+  if (n_rows == 0) return AGILE_OK;
+  if (!d_x || !d_y) return AGILE_EINVAL;
+  if (offsets_byte0 % kPage || cols_byte0 % kPage || vals_byte0 % kPage) return AGILE_EINVAL;
+  if (offsets_byte0 + ((uint64_t)n_rows + 1) * 8 > c->cfg.store_bytes) return AGILE_EINVAL;
+  if (cols_byte0 >= c->cfg.store_bytes || vals_byte0 >= c->cfg.store_bytes) return AGILE_EINVAL;
+  AGILE_CUDA_TRY(cudaSetDevice(c->device));
+  int r = ensure_slice_queue(c, std::min(cols_byte0, vals_byte0));
+  if (r) return r;
+  if (d_entries) AGILE_CUDA_TRY(cudaMemsetAsync(d_entries, 0, 8, as_stream(stream)));
+  SpmvApp app{offsets_byte0 / kPage, cols_byte0 / kPage, vals_byte0 / kPage, n_rows, d_x, n_cols, d_y,
+              (unsigned long long *)d_entries, mode, (HubEntry *)c->bfs_hubq, c->bfs_hub_cap,
+              g_bfs_epoch.fetch_add(1) & 0xFFFFFFFFull};
+  // each warp pins one page of each of three arrays and requests up to two units ahead
+  return launch_engine(c, app, stream, warps_for_cache(c, mode == AGILE_ASYNC ? 6 : 3, 32));
 }
 
 }  // extern "C"
