@@ -769,7 +769,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bfs", choices=["bfs", "embedding", "hits", "sweeps"])
+    ap.add_argument("--workload", default="bfs", choices=["bfs", "embedding", "hits", "sweeps", "spmv"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--wait-timeout-s", type=float, default=10.0,
@@ -810,6 +810,17 @@ def main():
             res["train"] = run_train(args, torch, ag, dev)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline_bfs(*graph)
+    elif args.workload == "spmv":
+        n, off, cols = synth.rmat_csr(3, 20, 16)
+        sp = run_spmv(args, torch, ag, dev, off, cols)
+        res = {"metric": "SpMV matrix entries/s (async), RMAT scale 20 through a 1/8 HBM cache",
+               "value": sp["async"]["entries_per_s"], "unit": "entries/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": sp["async"]["ms_per_call"], "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": sp["workload"]}, "sync": sp["sync"], "roofline": sp["async"]["roofline"]}
+        peak = measure_link_peak(torch, dev)
+        res["roofline"].update(peak=peak, unit="GB/s", frac=res["roofline"]["achieved"] / peak,
+                               peak_source="measured in this run: pinned host->HBM copy of 1 GiB (copy engine)")
     elif args.workload == "sweeps":
         res = {"metric": "async over sync speedup of the lookup + compute pipeline (sensitivity sweeps)",
                "unit": "x", "n_gpus": world, "data": "synthetic", "sweeps": run_sweeps(args, torch, ag, dev)}
