@@ -408,7 +408,10 @@ def run_spmv(args, torch, ag, dev, off, cols):
             st = ag.agile_stats(ctx)
             res[name] = {"entries_per_s": cols.size / t_call, "ms_per_call": t_call * 1e3,
                          "roofline": {"bound": "host_link", "achieved": algo / t_call / 1e9,
-                                      "algorithmic_bytes_per_launch": algo}}
+                                      "traffic": recorded_traffic("engine_kernel<SpmvApp>"),
+                                      "link_traffic": recorded_traffic("engine_kernel<SpmvApp>",
+                                                                       "link_bytes_per_launch"),
+                                      "kernel": "engine_kernel<SpmvApp>", "algorithmic_bytes_per_launch": algo}}
         err = ag.agile_check(ctx)
         if err:
             raise RuntimeError(f"device error: {ag.strerror(err)}")
