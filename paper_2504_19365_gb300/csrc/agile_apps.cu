@@ -436,7 +436,7 @@ struct BfsApp {
       uint64_t p = __shfl_sync(kFull, nxt, __ffs(m) - 1);
       release(d, pc);
       uint32_t line;
-      if (!warp_pin_page(d, p, a.q0, a.deadline, line)) return false;
+      if (!warp_pin_page<true>(d, p, a.q0, a.deadline, line)) return false;
       pc.page = p;
       pc.line = line;
       pc.valid = true;
@@ -601,8 +601,8 @@ struct BfsApp {
     uint32_t v = v0 + lane_id();
     uint64_t pa = off_page0 + ((uint64_t)v * 8) / kPage, pb = off_page0 + ((uint64_t)v * 8 + 8) / kPage;
     bool need_a = f && !(pc.valid && pc.page == pa), need_b = f && pb != pa && !(pc.valid && pc.page == pb);
-    if (__any_sync(kFull, need_a) && !warp_request(d, need_a, pa, a.q0, false, a.deadline)) return false;
-    if (__any_sync(kFull, need_b) && !warp_request(d, need_b, pb, a.q0, false, a.deadline)) return false;
+    if (__any_sync(kFull, need_a) && !warp_request_call(d, need_a, pa, a.q0, false, a.deadline)) return false;
+    if (__any_sync(kFull, need_b) && !warp_request_call(d, need_b, pb, a.q0, false, a.deadline)) return false;
     return true;
   }
 
@@ -623,8 +623,8 @@ struct BfsApp {
     uint64_t pb = col_page0 + ((uint64_t)(dg ? e - 1 : s) * 4) / kPage;
     bool want_a = dg && !(pc.valid && pc.page == pa);
     bool want_b = dg && pb != pa && !(pc.valid && pc.page == pb);
-    if (__any_sync(kFull, want_a) && !warp_request(d, want_a, pa, a.q0, false, a.deadline)) return false;
-    if (__any_sync(kFull, want_b) && !warp_request(d, want_b, pb, a.q0, false, a.deadline)) return false;
+    if (__any_sync(kFull, want_a) && !warp_request_call(d, want_a, pa, a.q0, false, a.deadline)) return false;
+    if (__any_sync(kFull, want_b) && !warp_request_call(d, want_b, pb, a.q0, false, a.deadline)) return false;
     return true;
   }
 
@@ -707,7 +707,7 @@ struct BfsApp {
         uint64_t q0p = col_page0 + ((uint64_t)p0 * 4) / kPage, q1p = col_page0 + ((uint64_t)(p1 - 1) * 4) / kPage;
         uint64_t pg = q0p + l;
         bool want = pg <= q1p && !(pc.valid && pc.page == pg);
-        if (__any_sync(kFull, want) && !warp_request(d, want, pg, a.q0, false, a.deadline)) return false;
+        if (__any_sync(kFull, want) && !warp_request_call(d, want, pg, a.q0, false, a.deadline)) return false;
       }
       for (int64_t b0 = p0; b0 < p1; b0 += 64) {
         bool on[2];
@@ -874,7 +874,7 @@ struct SpmvApp {
       if (warp_probe_pin(d, p, line) != P_HIT) {
         release(d, o1);
         release(d, o2);
-        if (!warp_pin_page(d, p, a.q0, a.deadline, line)) return false;
+        if (!warp_pin_page<true>(d, p, a.q0, a.deadline, line)) return false;
       }
       pc.page = p;
       pc.line = line;
@@ -1035,7 +1035,7 @@ struct SpmvApp {
     uint32_t vend = min(v0 + 32, n);
     uint64_t pa = off_page0 + ((uint64_t)v0 * 8) / kPage, pb = off_page0 + ((uint64_t)vend * 8) / kPage;
     bool want = (lane_id() == 0) || (lane_id() == 1 && pb != pa);
-    return warp_request(d, want, lane_id() == 0 ? pa : pb, a.q0, false, a.deadline);
+    return warp_request_call(d, want, lane_id() == 0 ? pa : pb, a.q0, false, a.deadline);
   }
 
   // stage B: read the offsets, queue long rows, request the unit's column and value pages
@@ -1062,8 +1062,8 @@ struct SpmvApp {
     if (hi <= lo) return true;
     uint64_t c0 = ((uint64_t)lo * 4) / kPage, c1 = ((uint64_t)(hi - 1) * 4) / kPage;
     bool want = c0 + lane_id() <= c1;
-    if (!warp_request(d, want, col_page0 + c0 + lane_id(), a.q0, false, a.deadline)) return false;
-    return warp_request(d, want, val_page0 + c0 + lane_id(), a.q0, false, a.deadline);
+    if (!warp_request_call(d, want, col_page0 + c0 + lane_id(), a.q0, false, a.deadline)) return false;
+    return warp_request_call(d, want, val_page0 + c0 + lane_id(), a.q0, false, a.deadline);
   }
 
   // take queued slices until every slice is taken (the BFS slice queue, one level)
@@ -1114,8 +1114,8 @@ struct SpmvApp {
       if (mode == AGILE_ASYNC) {
         uint64_t c0 = ((uint64_t)p0 * 4) / kPage, c1 = ((uint64_t)(p1 - 1) * 4) / kPage;
         bool want = c0 + l <= c1;
-        if (!warp_request(d, want, col_page0 + c0 + l, a.q0, false, a.deadline)) return false;
-        if (!warp_request(d, want, val_page0 + c0 + l, a.q0, false, a.deadline)) return false;
+        if (!warp_request_call(d, want, col_page0 + c0 + l, a.q0, false, a.deadline)) return false;
+        if (!warp_request_call(d, want, val_page0 + c0 + l, a.q0, false, a.deadline)) return false;
       }
       float sum = 0.0f;  // the slice's running sum (the same in every lane)
       for (int64_t b0 = p0; b0 < p1; b0 += 32) {
@@ -1221,9 +1221,10 @@ int bfs_launch(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32
   BfsApp app{offsets_byte0 / kPage, cols_byte0 / kPage, n_vertices, d_level,
              (unsigned long long *)d_edges_scanned, mode, hubq, hub_cap,
              g_bfs_epoch.fetch_add(1) & 0xFFFFFFFFull, vis};
-  // sync: about two lines per warp (one pinned, one being filled); async: four, since a
-  // warp also holds the pages it requested for its next units
-  return launch_engine(c, app, stream, warps_for_cache(c, mode == AGILE_ASYNC ? 4 : 2, 32));
+  // sync: about two lines per warp (one pinned, one being filled); async: three, since a
+  // warp also has the pages of its next unit requested (measured best against two and
+  // four at a cache of an eighth of the column array)
+  return launch_engine(c, app, stream, warps_for_cache(c, mode == AGILE_ASYNC ? 3 : 2, 32));
 }
 
 // ---------------------------------------------------------------- BFS without allocation

@@ -703,6 +703,16 @@ __device__ __forceinline__ int warp_probe_pin(const Dev &d, uint64_t page, uint3
 // The warp needs one page pinned (uniform `page`): probe with a pin; on a miss the warp
 // issues and waits with nothing pinned, then probes again.  Returns the line in every
 // lane, or false on timeout/abort.  The caller unpins it (one unpin per pin).
+// warp_request as one out-of-line copy: for applications whose code is large (many call
+// sites of the miss path next to the service code), one shared copy keeps their hot
+// loops small (fewer spills, fewer instruction-cache misses); a call costs little next
+// to the round trips of a request
+static __device__ __noinline__ bool warp_request_call(const Dev &d, bool want, uint64_t page, uint32_t q0,
+                                                      bool wait, uint64_t deadline) {
+  return warp_request(d, want, page, q0, wait, deadline);
+}
+
+template <bool kCall = false>
 static __device__ bool warp_pin_page(const Dev &d, uint64_t page, uint32_t q0, uint64_t deadline,
                               uint32_t &line_out) {
   for (int round = 0;; ++round) {
@@ -713,7 +723,9 @@ static __device__ bool warp_pin_page(const Dev &d, uint64_t page, uint32_t q0, u
       if (lane_id() == 0 && round == 0) atomicAdd(stat_ptr(d, S_HITS), 1ull);
       return true;
     }
-    if (!warp_request(d, lane_id() == 0, page, q0, true, deadline)) return false;
+    if (!(kCall ? warp_request_call(d, lane_id() == 0, page, q0, true, deadline)
+                : warp_request(d, lane_id() == 0, page, q0, true, deadline)))
+      return false;
     if (aborted(d)) return false;
     if (gtimer() > deadline) {
       if (lane_id() == 0) set_error(d, -110);
