@@ -72,3 +72,19 @@ def test_sqe_and_cqe_layout_constants():
     src = open(os.path.join(ROOT, "paper_2504_19365_gb300", "csrc", "agile_dev.cuh")).read()
     assert "struct alignas(64) Sqe { uint32_t dw[16]; };" in src
     assert "struct alignas(16) Cqe { uint32_t dw[4]; };" in src
+
+
+def test_application_calls_reject_a_missing_context(libpath):
+    # every application entry point validates its arguments on the host before it
+    # touches a device
+    import paper_2504_19365_gb300 as ag
+    L = ag.lib()
+    E = ag.AGILE_EINVAL
+    assert L.agile_embedding_bag(None, 0, 10, 128, None, None, 1, None, 0, None) == E
+    assert L.agile_embedding_bag_backward(None, 0, 10, 128, None, None, 1, 1, None, 0.0, None, 0, None) == E
+    assert L.agile_embedding_pipeline(None, 0, 4096, 1, 10, 64, None, 1, 1, 1, 0, None, 0, None) == E
+    assert L.agile_bfs(None, 0, 4096, 10, 0, None, None, 0, None) == E
+    assert L.agile_bfs_noalloc(None, 0, 4096, 10, 10, 0, None, None, 0, None) == E
+    assert L.agile_spmv(None, 0, 4096, 8192, 10, 10, None, None, None, 0, None) == E
+    # an invalid mode is rejected the same way
+    assert L.agile_spmv(None, 0, 4096, 8192, 10, 10, None, None, None, 7, None) == E
