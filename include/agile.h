@@ -215,7 +215,9 @@ AGILE_API int agile_embedding_pipeline(agile_ctx *ctx, uint64_t table_byte0, uin
  * [n_vertices+1] at byte offsets_byte0, int32 columns at byte cols_byte0 (both
  * multiples of 4096).  d_level[v] = BFS level of v from src, -1 when unreachable.
  * *d_edges_scanned (uint64, device, may be NULL) = sum of the degrees of every
- * reached vertex.  Top-down, level-synchronous; mode as above. */
+ * reached vertex.  Top-down, level-synchronous.  AGILE_SYNC requests every page when
+ * it is needed; AGILE_ASYNC also requests all pages of a slice of a long adjacency
+ * list before scanning it (a warp's own vertices as in AGILE_SYNC). */
 AGILE_API int agile_bfs(agile_ctx *ctx, uint64_t offsets_byte0, uint64_t cols_byte0,
               uint32_t n_vertices, int32_t src, int32_t *d_level,
               uint64_t *d_edges_scanned, uint32_t mode, void *stream);

@@ -346,10 +346,10 @@ struct PipeApp {
 // the grid barrier that ends the level; the search stops when a level discovers
 // nothing.  Edges scanned = sum of the degrees of the frontier vertices of all levels.
 //   SYNC : each page (offsets, columns) is requested when needed and waited for.
-//   ASYNC: a three-stage software pipeline over 32-vertex units: while the warp scans
-//          unit i, the offsets of unit i+1 are read and the pages of its lists are
-//          issued, and the offsets pages of unit i+2 are issued; a long-list slice
-//          issues all of its pages before it is scanned.
+//   ASYNC: as SYNC for a warp's own vertices, and a long-list slice requests all of its
+//          pages before it is scanned, so that their fetches overlap.  (Requesting the
+//          pages of the next units ahead as well was measured slower with the cache at
+//          an eighth of the column array: those pages were evicted before their use.)
 // A warp keeps at most one line pinned between steps (the page it read last) and lets
 // it go before it requests or waits for any other page.
 // One slice (at most kSlice entries) of a long adjacency list, queued for any warp.
@@ -561,7 +561,7 @@ struct BfsApp {
     return true;
   }
 
-  // synchronous processing of one 32-vertex unit: every page when needed
+  // one 32-vertex unit: every page when needed
   __device__ bool chunk(const Dev &d, const AppCtx &a, uint32_t v0, int32_t L, uint32_t &found,
                         unsigned long long &scanned, Pin &pc) const {
     uint32_t v = v0 + lane_id();
@@ -573,89 +573,6 @@ struct BfsApp {
     scanned += __reduce_add_sync(kFull, deg);
     bool hub = push_hub(d, deg, s, e, L);
     return scan_lists(d, a, s, hub ? 0 : deg, L, found, pc);
-  }
-
-  // ---- asynchronous pipeline over 32-vertex units (ASYNC mode) ---------------------
-  // Next unit of this warp with at least one frontier vertex; chunks of kChunk ids are
-  // claimed from the level's counter as needed.
-  __device__ bool next_unit(const Dev &d, int32_t L, uint32_t nchunks, uint32_t &chunk, uint32_t &sub,
-                            uint32_t &v0, bool &f) const {
-    for (;;) {
-      if (sub >= kChunk) {
-        uint32_t c = 0;
-        if (lane_id() == 0) c = atomicAdd(&d.run->work[L & 1], 1u);
-        chunk = __shfl_sync(kFull, c, 0);
-        sub = 0;
-        if (chunk >= nchunks || aborted(d)) return false;
-      }
-      v0 = chunk * kChunk + sub;
-      sub += 32;
-      uint32_t v = v0 + lane_id();
-      f = v < n && ld_rlx32((const uint32_t *)&level[v]) == (uint32_t)L;
-      if (__any_sync(kFull, f)) return true;
-    }
-  }
-
-  // stage A: issue the offsets pages of a unit
-  __device__ bool stage_a(const Dev &d, const AppCtx &a, uint32_t v0, bool f, const Pin &pc) const {
-    uint32_t v = v0 + lane_id();
-    uint64_t pa = off_page0 + ((uint64_t)v * 8) / kPage, pb = off_page0 + ((uint64_t)v * 8 + 8) / kPage;
-    bool need_a = f && !(pc.valid && pc.page == pa), need_b = f && pb != pa && !(pc.valid && pc.page == pb);
-    if (__any_sync(kFull, need_a) && !warp_request_call(d, need_a, pa, a.q0, false, a.deadline)) return false;
-    if (__any_sync(kFull, need_b) && !warp_request_call(d, need_b, pb, a.q0, false, a.deadline)) return false;
-    return true;
-  }
-
-  // stage B: read the offsets, queue long lists, issue the unit's column span; returns the
-  // start and the degree left to scan here (0 for queued long lists)
-  __device__ bool stage_b(const Dev &d, const AppCtx &a, uint32_t v0, bool f, int32_t L, int64_t &s, uint32_t &dg,
-                          unsigned long long &scanned, Pin &pc) const {
-    uint32_t v = v0 + lane_id();
-    int64_t e = 0;
-    s = 0;
-    if (!read_offsets(d, a, v, f, s, e, pc)) return false;
-    uint32_t deg = f ? (uint32_t)(e - s) : 0;
-    scanned += __reduce_add_sync(kFull, deg);
-    bool hub = push_hub(d, deg, s, e, L);
-    dg = hub ? 0 : deg;
-    // a list shorter than kHub entries spans at most two pages: issue exactly those
-    uint64_t pa = col_page0 + ((uint64_t)s * 4) / kPage;
-    uint64_t pb = col_page0 + ((uint64_t)(dg ? e - 1 : s) * 4) / kPage;
-    bool want_a = dg && !(pc.valid && pc.page == pa);
-    bool want_b = dg && pb != pa && !(pc.valid && pc.page == pb);
-    if (__any_sync(kFull, want_a) && !warp_request_call(d, want_a, pa, a.q0, false, a.deadline)) return false;
-    if (__any_sync(kFull, want_b) && !warp_request_call(d, want_b, pb, a.q0, false, a.deadline)) return false;
-    return true;
-  }
-
-  // stage C: scan the unit's lists (flattened over the warp)
-  __device__ bool stage_c(const Dev &d, const AppCtx &a, int64_t s, uint32_t dg, int32_t L, uint32_t &found,
-                          Pin &pc) const {
-    return scan_lists(d, a, s, dg, L, found, pc);
-  }
-
-  __device__ bool run_async_units(const Dev &d, const AppCtx &a, int32_t L, uint32_t nchunks, uint32_t &found,
-                                  unsigned long long &scanned, Pin &pc) const {
-    uint32_t chunk = 0, sub = kChunk;
-    uint32_t v1 = 0, v2 = 0;
-    bool f1 = false, f2 = false;
-    int64_t s0 = 0, s1 = 0;
-    uint32_t dg0 = 0, dg1 = 0;
-    bool have0 = false, have1 = next_unit(d, L, nchunks, chunk, sub, v1, f1), have2 = false;
-    if (have1 && !stage_a(d, a, v1, f1, pc)) return false;
-    for (;;) {
-      have2 = have1 && next_unit(d, L, nchunks, chunk, sub, v2, f2);
-      if (have2 && !stage_a(d, a, v2, f2, pc)) return false;
-      if (have1 && !stage_b(d, a, v1, f1, L, s1, dg1, scanned, pc)) return false;
-      if (have0 && !stage_c(d, a, s0, dg0, L, found, pc)) return false;
-      have0 = have1;
-      s0 = s1;
-      dg0 = dg1;
-      have1 = have2;
-      v1 = v2;
-      f1 = f2;
-      if (!have0 && !have1) return true;
-    }
   }
 
   // Take queued slices of level L, one ticket (a record index) at a time, until every
@@ -743,17 +660,13 @@ struct BfsApp {
       uint32_t found = 0;
       Pin pc{0, 0, false};
       bool ok = true;
-      if (mode == AGILE_ASYNC) {
-        ok = run_async_units(d, a, L, nchunks, found, scanned, pc);
-      } else {
-        for (;;) {
-          uint32_t c = 0;
-          if (l == 0) c = atomicAdd(&d.run->work[L & 1], 1u);
-          c = __shfl_sync(kFull, c, 0);
-          if (c >= nchunks || aborted(d)) break;
-          for (uint32_t sub = 0; sub < kChunk && ok; sub += 32) ok = chunk(d, a, c * kChunk + sub, L, found, scanned, pc);
-          if (!ok) break;
-        }
+      for (;;) {
+        uint32_t c = 0;
+        if (l == 0) c = atomicAdd(&d.run->work[L & 1], 1u);
+        c = __shfl_sync(kFull, c, 0);
+        if (c >= nchunks || aborted(d)) break;
+        for (uint32_t sub = 0; sub < kChunk && ok; sub += 32) ok = chunk(d, a, c * kChunk + sub, L, found, scanned, pc);
+        if (!ok) break;
       }
       // this warp queues no more slices of level L
       __syncwarp();
@@ -1221,10 +1134,9 @@ int bfs_launch(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32
   BfsApp app{offsets_byte0 / kPage, cols_byte0 / kPage, n_vertices, d_level,
              (unsigned long long *)d_edges_scanned, mode, hubq, hub_cap,
              g_bfs_epoch.fetch_add(1) & 0xFFFFFFFFull, vis};
-  // sync: about two lines per warp (one pinned, one being filled); async: three, since a
-  // warp also has the pages of its next unit requested (measured best against two and
-  // four at a cache of an eighth of the column array)
-  return launch_engine(c, app, stream, warps_for_cache(c, mode == AGILE_ASYNC ? 3 : 2, 32));
+  // about two lines per warp (one pinned, one being filled; a slice's requested pages are
+  // scanned right away)
+  return launch_engine(c, app, stream, warps_for_cache(c, 2, 32));
 }
 
 // ---------------------------------------------------------------- BFS without allocation
