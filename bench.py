@@ -627,6 +627,57 @@ def run_sweeps(args, torch, ag, dev):
     return out
 
 
+def run_bfs_cache_sweep(args, torch, ag, dev):
+    """BFS (RMAT scale 20, 8 sources, each from an invalidated cache with L2 flushed) at
+    HBM caches of 1/16 to 1/1 of the column array, sync and async: edges/s, the pages the
+    device moved per BFS and the link rate they make."""
+    n, off, cols = synth.rmat_csr(3, 20, 16)
+    srcs = synth.bfs_sources(3, off, 8)
+    col0 = round_page(off.nbytes)
+    total = col0 + round_page(cols.nbytes)
+    stream = torch.cuda.current_stream().cuda_stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    level = torch.empty(n, dtype=torch.int32, device=dev)
+    edges = torch.zeros(1, dtype=torch.int64, device=dev)
+    link_peak = measure_link_peak(torch, dev)
+    out = {"workload": "RMAT scale 20 BFS, 8 sources, cold cache per BFS", "link_peak_gbs": link_peak}
+    for frac in (16, 8, 4, 2, 1):
+        cache = max(8 * PAGE, (cols.nbytes // frac + 8 * PAGE - 1) // (8 * PAGE) * (8 * PAGE))
+        cfg = ag.agile_config_default(store_bytes=total, cache_bytes=cache, ways=8, device=torch.cuda.current_device(),
+                                      wait_timeout_ns=int(args.wait_timeout_s * 1e9))
+        ctx = ag.agile_init(cfg)
+        try:
+            ag.agile_store_write(ctx, 0, off.ctypes.data, off.nbytes)
+            ag.agile_store_write(ctx, col0, cols.ctypes.data, cols.nbytes)
+            pt = {"cache_bytes": cache}
+            for mode, name in ((ag.AGILE_ASYNC, "async"), (ag.AGILE_SYNC, "sync")):
+                ms, work = 0.0, 0
+                for rep in range(2):
+                    if rep:
+                        ag.agile_reset_stats(ctx)
+                    for s in srcs:
+                        ag.agile_invalidate(ctx, stream)
+                        flush.zero_()
+                        t = timed(torch, lambda: ag.agile_bfs(ctx, 0, col0, n, int(s), level.data_ptr(),
+                                                              edges.data_ptr(), mode, stream))
+                        if rep:
+                            ms += t
+                            work += int(edges.item())
+                st = ag.agile_stats(ctx)
+                moved = st["bytes_read"] / len(srcs)
+                t_bfs = ms / len(srcs) * 1e-3
+                pt[name] = {"edges_per_s": work / (ms * 1e-3), "ms_per_bfs": round(t_bfs * 1e3, 3),
+                            "moved_mb_per_bfs": round(moved / 1e6, 1),
+                            "moved_link_frac": moved / t_bfs / 1e9 / link_peak}
+            err = ag.agile_check(ctx)
+            if err:
+                raise RuntimeError(f"device error: {ag.strerror(err)}")
+            out[f"1/{frac}"] = pt
+        finally:
+            ag.agile_destroy(ctx)
+    return out
+
+
 def run_serving(torch, ag, dev, ctx, nt, rows, dim, stride, stream, n_req=600):
     sizes = np.minimum(4096, np.maximum(1, np.round(2.0 ** (synth.uniform01(7, n_req) * 12)))).astype(int)
     pools = synth.uniform_int(8, n_req, 64) + 1
@@ -826,7 +877,8 @@ def main():
                                peak_source="measured in this run: pinned host->HBM copy of 1 GiB (copy engine)")
     elif args.workload == "sweeps":
         res = {"metric": "async over sync speedup of the lookup + compute pipeline (sensitivity sweeps)",
-               "unit": "x", "n_gpus": world, "data": "synthetic", "sweeps": run_sweeps(args, torch, ag, dev)}
+               "unit": "x", "n_gpus": world, "data": "synthetic", "sweeps": run_sweeps(args, torch, ag, dev),
+               "bfs_cache": run_bfs_cache_sweep(args, torch, ag, dev)}
     elif args.workload == "hits":
         h = run_hits(args, torch, ag, dev)
         res = {"metric": "embedding-bag lookups/s, all cache hits (sync)", "value": h["sync"]["lookups_per_s"],
