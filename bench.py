@@ -851,7 +851,10 @@ def main():
     _b.build()  # no-op when up to date
     if args.workload == "bfs":
         res, graph = run_bfs(args, torch, ag, dev, rank, world)
-        if not args.no_extras:
+        # the other workloads are reported by single-GPU runs (a multi-rank run measures
+        # the replicated headline only; the config-3 tables alone pin 20 GB of host
+        # memory per rank)
+        if not args.no_extras and world == 1:
             res["spmv"] = run_spmv(args, torch, ag, dev, graph[0], graph[1])
             peak = res["roofline"]["peak"]
             for m in ("async", "sync"):
