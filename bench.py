@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -56,11 +57,16 @@ def round_page(n):
 
 
 def csrc_hash() -> str:
+    """Hash of the library's compiled content: the CUDA/C++ sources and the header with
+    their comments and whitespace removed (an edit of a comment leaves it unchanged)."""
     h = hashlib.sha256()
     for d in ("paper_2504_19365_gb300/csrc", "include"):
         for f in sorted(os.listdir(os.path.join(ROOT, d))):
-            with open(os.path.join(ROOT, d, f), "rb") as fh:
-                h.update(f.encode() + fh.read())
+            with open(os.path.join(ROOT, d, f), encoding="utf-8") as fh:
+                src = fh.read()
+            src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+            src = re.sub(r"//[^\n]*", " ", src)
+            h.update(f.encode() + " ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

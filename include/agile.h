@@ -14,9 +14,12 @@
  *   - an in-flight share table (page -> request in flight) [Sec. 3.4.1];
  *   - issue / continue / wait with completion tokens: no thread waits for a completion
  *     while it holds a queue slot or a cache line [Sec. 2.3.1, Sec. 2.3.2, Sec. 3.2.1];
- *   - two drivers: sum-pooled embedding-bag lookups [Sec. 4.4] and a CSR breadth-first
- *     search [Sec. 4.5], each in a synchronous mode (issue then stall) and an
- *     asynchronous mode (issue ahead, continue, wait later) [Sec. 4.2, Sec. 4.4].
+ *   - drivers: sum-pooled embedding-bag lookups [Sec. 4.4], a CSR breadth-first search
+ *     and an SpMV over the same CSR layout [Sec. 4.5], each in a synchronous mode
+ *     (issue then stall) and an asynchronous mode (issue ahead, continue, wait later)
+ *     [Sec. 4.2, Sec. 4.4]; the embedding bag also has a backward pass with an SGD
+ *     step written back through the queues, a lookup + compute pipeline and a
+ *     continuous-batching serving loop.
  *
  * The backing store is an emulated NVMe device: its data lives in pinned host memory
  * (reached over the host link), it consumes the 64-byte submission entries from the
@@ -24,7 +27,9 @@
  * completion entries with a phase bit.  Its latency and per-queue throughput are
  * configurable.  The device is emulated by warps of the same kernel launch that runs
  * the work, so it makes progress only while a library call is executing on the GPU;
- * every call drains the commands it issued before it returns on its stream.
+ * every call drains the commands it issued before it returns on its stream.  When the
+ * cache leaves enough application warps of a launch idle, those warps poll the
+ * completion queues (one queue each) instead.
  *
  * Conventions
  *   - Ownership: the library owns the cache, queues, tokens, staging buffers and the
