@@ -90,3 +90,24 @@ def test_rmat_scale20_config_parity():
                 assert np.array_equal(got, want)
                 assert edges == scanned
         assert_cache_invariants(c)
+
+
+@pytest.mark.parametrize("mode", [ag.AGILE_SYNC, ag.AGILE_ASYNC])
+def test_tiny_ring_and_tiny_cache(mode):
+    # one queue of depth 64 and an 8-line cache: every warp must let its pin go before
+    # it waits, or the search could not finish
+    n, off, cols = synth.rmat_csr(31, 10, 8)
+    col0 = round_page(off.nbytes)
+    total = col0 + round_page(cols.nbytes)
+    src = int(synth.bfs_sources(31, off, 1)[0])
+    want, scanned = oracle.bfs(off, cols, src)
+    with Ctx(total, cache_bytes=8 * 4096, ways=2, num_queues=1, queue_depth=64) as c:
+        c.put(0, off)
+        c.put(col0, cols)
+        lv = torch.empty(n, dtype=torch.int32, device=DEV)
+        ed = torch.zeros(1, dtype=torch.int64, device=DEV)
+        ag.agile_bfs(c.h, 0, col0, n, src, lv.data_ptr(), ed.data_ptr(), mode, c.stream)
+        torch.cuda.synchronize()
+        c.check()
+        assert np.array_equal(lv.cpu().numpy(), want) and int(ed.item()) == scanned
+        assert_cache_invariants(c)

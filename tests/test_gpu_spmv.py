@@ -154,3 +154,19 @@ def test_full_rmat20_against_oracle():
             c.check()
             _check(off, cols, vals, x, y)
             assert ent == cols.size
+
+
+@pytest.mark.parametrize("mode", [ag.AGILE_SYNC, ag.AGILE_ASYNC])
+def test_tiny_ring_and_tiny_cache(mode):
+    # one queue of depth 64 and an 8-line cache while warps pin pages of three arrays:
+    # a warp that has to wait lets all of its pins go first
+    n, off, cols = synth.rmat_csr(32, 10, 8)
+    vals = ((synth.uniform_int(33, cols.size, 32) - 16) / 4.0).astype(np.float32)
+    x = ((synth.uniform_int(34, n, 32) - 16) / 4.0).astype(np.float32)
+    _, _, total = _layout(off, cols, vals)
+    with Ctx(total, cache_bytes=8 * 4096, ways=2, num_queues=1, queue_depth=64) as c:
+        col0, val0 = _store(c, off, cols, vals)
+        y, ent = _spmv(c, off, cols, vals, x, mode, col0, val0)
+        c.check()
+        assert np.array_equal(y.view(np.uint32), oracle.spmv(off, cols, vals, x).view(np.uint32))
+        assert ent == cols.size
