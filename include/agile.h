@@ -104,7 +104,27 @@ typedef struct {
   uint32_t prefetch_depth;  /* async lookahead in work units (0 = default 1)          */
   uint32_t app_warps;       /* cap on application warps per call (0 = sized from the
                                cache so the warps' working set fits in it)           */
+  uint32_t trace_records;   /* capacity of the device's command trace (0 = off); see
+                               agile_trace                                           */
+  uint32_t num_devices;     /* backing devices, 0 or 1 = one (Sec. 4.3): store page p
+                               lives on device p mod n as its block p / n, and queue q
+                               belongs to device q mod n (num_queues must be a
+                               multiple of n), so requests interleave over devices  */
+  uint32_t cache_policy;    /* AGILE_POLICY_CLOCK (default) or AGILE_POLICY_FIFO      */
+  double emu_device_read_gbps;   /* per-device read throughput cap, GB/s (0 = none)  */
+  double emu_device_write_gbps;  /* per-device write throughput cap, GB/s (0 = none) */
 } agile_config;
+
+/* Replacement policies of the cache (Sec. 3.4 leaves the policy to the user; Sec. 4.4
+ * uses clock).  Both pick a victim within the page's set starting at the set's hand and
+ * skip ways that are in flight, pinned or being written back; an INVALID way is always
+ * taken first (the lowest one).
+ *   CLOCK: a way whose reference bit is set (by a hit, or by its fill) has it cleared
+ *          and is passed over once.
+ *   FIFO : the reference bit is ignored: the way at the hand is the victim, so (with
+ *          nothing pinned or in flight) lines leave in the order they were filled. */
+#define AGILE_POLICY_CLOCK 0u
+#define AGILE_POLICY_FIFO 1u
 
 typedef struct {
   uint64_t hits;            /* requests served by a READY/MODIFIED line (case a)      */
@@ -234,10 +254,11 @@ AGILE_API int agile_bfs(agile_ctx *ctx, uint64_t offsets_byte0, uint64_t cols_by
  * the cache.  d_x: float [n_cols] and d_y: float [n_rows], device memory of the
  * caller (16-byte alignment not required).  d_y[v] = sum over j in
  * [offsets[v], offsets[v+1]) of vals[j] * x[cols[j]] in FP32, each product rounded
- * before it is added.  A row of fewer than 1024 entries is summed in increasing j
- * (equal bit for bit to that order); a longer row is summed in slices of 2048 entries,
- * each in increasing j, whose sums are added in the order they finish.  A column
- * number >= n_cols contributes 0 and records AGILE_EINVAL (agile_check).
+ * before it is added, added in increasing j from +0 (equal bit for bit to that order
+ * in every row: a row of 1024 entries or more is cut into slices of 1024 whose products
+ * are computed in parallel, and each slice continues the running sum of the one
+ * before).  A column number >= n_cols contributes 0 and records AGILE_EINVAL
+ * (agile_check).
  * *d_entries (uint64, device, may be NULL) = number of entries (offsets[n_rows] -
  * offsets[0]).  mode as above.  Uses the library's slice-queue scratch (shared with
  * agile_bfs; allocated on first use). */
@@ -245,18 +266,41 @@ AGILE_API int agile_spmv(agile_ctx *ctx, uint64_t offsets_byte0, uint64_t cols_b
                          uint32_t n_rows, uint32_t n_cols, const float *d_x, float *d_y,
                          uint64_t *d_entries, uint32_t mode, void *stream);
 
+/* Step 1 of the Sec. 4.5 three-step breakdown ("kernel time": the application kernel
+ * with the graph in HBM, read with plain loads): the BFS of agile_bfs, the same kernel
+ * and launch, over a CSR held in device memory of the caller instead of the store --
+ * d_offsets int64 [n_vertices+1], d_cols int32 [n_cols] -- without the cache or the
+ * queues.  Results as agile_bfs.  With agile_bfs on a cache preloaded with the whole
+ * graph (step 3, cache API time) and on a cold cache (step 2, I/O API time) it splits
+ * a BFS's time into kernel, cache and I/O parts.  Uses the context's launch shape and
+ * BFS scratch (allocated on first use). */
+AGILE_API int agile_bfs_hbm(agile_ctx *ctx, const int64_t *d_offsets, const int32_t *d_cols, uint32_t n_vertices,
+                            uint64_t n_cols, int32_t src, int32_t *d_level, uint64_t *d_edges_scanned,
+                            void *stream);
+
+/* Step 1 of the Sec. 4.5 breakdown for agile_spmv: the same kernel over a CSR held in
+ * device memory (d_offsets int64 [n_rows+1], d_cols int32 and d_vals float [n_entries]),
+ * without the cache or the queues; results equal agile_spmv's bit for bit. */
+AGILE_API int agile_spmv_hbm(agile_ctx *ctx, const int64_t *d_offsets, const int32_t *d_cols, const float *d_vals,
+                             uint32_t n_rows, uint32_t n_cols, uint64_t n_entries, const float *d_x, float *d_y,
+                             uint64_t *d_entries, void *stream);
+
 /* BFS exactly as agile_bfs, for callers that cannot allocate device memory during the
- * call (code being captured into a CUDA graph, latency-critical loops where an
- * allocation's device synchronisation is not acceptable).  The paper has no
- * counterpart: it is an addition of this library.  agile_bfs allocates a queue of long
- * adjacency lists and a visited bitmap on first use; this entry point uses fixed device
- * arrays compiled into the library instead (1 MiB and 4 MiB) and calls no
- * cudaMalloc/cudaFree.  n_cols: number of int32 column entries of the graph; graphs
- * with more than 33,553,408 column entries (32,768 queue slots of 1,024 entries) or
- * more than 33,554,432 vertices are rejected with AGILE_EINVAL and a message on
- * stderr.  The first call on a device looks up the arrays' device addresses (make that
- * first call before any stream capture).  All calls on a device share the arrays:
- * calls of this entry point that overlap on one GPU race. */
+ * call: code running under stream capture (where cudaMalloc is not allowed), or a
+ * latency-critical loop where the device synchronisation that an allocation implies
+ * would stall other streams.  The paper has no counterpart: it is an addition of this
+ * library.  agile_bfs allocates a queue of long adjacency lists and a visited bitmap on
+ * first use; this entry point uses fixed device arrays compiled into the library
+ * instead (2 MiB and 4 MiB, held by every GPU that loads the library until the process
+ * exits) and calls no cudaMalloc/cudaFree.  n_cols: number of int32 column entries of
+ * the graph; graphs with more than 33,553,408 column entries (32,768 queue slots of
+ * 1,024 entries) or more than 33,554,432 vertices are rejected with AGILE_EINVAL and a
+ * message on stderr.  The first call on a device looks up the arrays' device addresses
+ * (make that first call before any stream capture); the addresses are kept for the
+ * process, so a device reset (cudaDeviceReset) between calls is not supported.  All
+ * calls on a device share the arrays: calls of this entry point that overlap on one GPU
+ * race.  Queue records from an earlier call never need clearing: each record is
+ * published with a number the device draws for every kernel execution. */
 AGILE_API int agile_bfs_noalloc(agile_ctx *ctx, uint64_t offsets_byte0, uint64_t cols_byte0,
                                 uint32_t n_vertices, uint64_t n_cols, int32_t src, int32_t *d_level,
                                 uint64_t *d_edges_scanned, uint32_t mode, void *stream);
@@ -313,6 +357,63 @@ AGILE_API uint32_t agile_cache_sets(agile_ctx *ctx);
 /* Counters since init or the last reset (synchronises the device). */
 AGILE_API int agile_stats(agile_ctx *ctx, agile_stats_t *out);
 AGILE_API int agile_reset_stats(agile_ctx *ctx);
+
+/* Change the emulated device model of a context between calls (the device must be
+ * idle: synchronises it first): number of backing devices (0 = 1; num_queues must be a
+ * multiple), per-command latency, per-queue cap and per-device read/write caps, with
+ * the meaning of the agile_config fields of the same names.  Store contents and cached
+ * lines are unaffected; where a page lives only decides which queues serve it. */
+AGILE_API int agile_set_device_model(agile_ctx *ctx, uint32_t num_devices, uint32_t emu_latency_ns,
+                                     double emu_queue_gbps, double emu_device_read_gbps,
+                                     double emu_device_write_gbps);
+
+/* Per-page accounting of the emulated device since init or the last agile_reset_stats
+ * (synchronises the device).  For store pages page0 .. page0+n-1, any of the host arrays
+ * may be NULL:
+ *   reads[i]   read commands the device served for the page (store -> HBM),
+ *   writes[i]  write commands it served for the page (HBM -> store),
+ *   dirtied[i] dirty epochs of the page: times a clean cache line of it turned MODIFIED
+ *              or a page write (agile_write_async) was started.
+ * Every dirty epoch ends in exactly one write (Sec. 3.4 case (d)): after agile_flush,
+ * writes[i] == dirtied[i] for every page.  AGILE_EINVAL if the range leaves the store. */
+AGILE_API int agile_page_io(agile_ctx *ctx, uint64_t page0, uint64_t n, uint32_t *host_reads,
+                            uint32_t *host_writes, uint32_t *host_dirtied);
+
+/* One command as the emulated device served it; times are the GPU's global timer in ns. */
+typedef struct {
+  uint64_t page;     /* store page                                                      */
+  uint64_t t_seen;   /* doorbell that exposed the command first read by the device (0 when
+                        the device has no latency or throughput model)                  */
+  uint64_t t_start;  /* an engine took the command; its data moves from here            */
+  uint64_t t_done;   /* its completion entry was posted                                 */
+  uint32_t q, cid, opcode, status;  /* queue, command id, 0 flush/no-op 1 write 2 read,
+                                       NVMe status (bit 16: completion dropped by the
+                                       fault injector)                                  */
+  uint32_t pad[4];
+} agile_trace_rec;
+
+/* Copy the device's command trace (cfg.trace_records > 0) to host: up to `cap` records
+ * into host_out, in the order engines took them; *n_out = records logged since init or
+ * the last agile_reset_stats (may exceed the trace's capacity; later ones are dropped).
+ * Synchronises the device. */
+AGILE_API int agile_trace(agile_ctx *ctx, agile_trace_rec *host_out, uint32_t cap, uint32_t *n_out);
+
+/* Host-link read bandwidth as the emulated device's engines see it: a kernel of
+ * `ctas` CTAs (0 = two per SM) streams `bytes` (a multiple of 4096) from the context's
+ * pinned store into d_dst with 16-byte loads, `reps` times; *gbps_out = best rate.
+ * A measurement aid, not part of the paper's method. */
+AGILE_API int agile_link_probe(agile_ctx *ctx, void *d_dst, uint64_t bytes, uint32_t ctas, uint32_t reps,
+                               double *gbps_out);
+
+/* For user kernels launched by agile_device.cuh (agile::launch_user): copy the
+ * context's device view (the library's agile::Dev: addresses of the cache, queues and
+ * device model) into *out, which has `size` bytes; AGILE_EINVAL unless size equals the
+ * library's view (a header of another version).  Makes the device current. */
+AGILE_API int agile_device_view(agile_ctx *ctx, void *out, uint64_t size);
+
+/* For agile::launch_user: zero the context's per-launch state and number the launch, on
+ * `stream`, right before a user launch. */
+AGILE_API int agile_run_reset(agile_ctx *ctx, void *stream);
 
 /* Synchronise the device and return the first error recorded on the GPU since the
  * last agile_check (0 if none), clearing it. */

@@ -50,6 +50,7 @@ def lib():
         L.orc_cache_new.argtypes = [u32, u32, u64]
         L.orc_cache_new.restype = vp
         L.orc_cache_free.argtypes = [vp]
+        L.orc_cache_set_policy.argtypes = [vp, C.c_int]
         L.orc_cache_lookup.argtypes = [vp, vp, u64, C.POINTER(u32), C.POINTER(u64)]
         L.orc_cache_lookup.restype = C.c_int
         L.orc_cache_read.argtypes = [vp, vp, u64, u32, u32, vp]
@@ -110,10 +111,13 @@ class RefCache:
     """Sequential reference cache; ``store`` is a uint8 numpy array the cache reads on
     fills and writes on write-backs (it is modified in place)."""
 
-    def __init__(self, sets: int, ways: int, store: np.ndarray, wb_cap: int = 1 << 20):
+    CLOCK, FIFO = 0, 1
+
+    def __init__(self, sets: int, ways: int, store: np.ndarray, wb_cap: int = 1 << 20, policy: int = 0):
         assert store.dtype == np.uint8 and store.flags.c_contiguous
         self.sets, self.ways, self.store = sets, ways, store
         self.h = lib().orc_cache_new(sets, ways, wb_cap)
+        lib().orc_cache_set_policy(self.h, policy)
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -68,7 +68,15 @@ typedef struct {
   uint64_t hits, misses, evictions, writebacks;
   uint64_t *wb_log; /* pages written back, in order                         */
   uint64_t wb_cap, wb_len;
+  int policy;       /* ORC_POLICY_CLOCK or ORC_POLICY_FIFO                 */
+  uint64_t *filled; /* [sets*ways] order in which the way was last filled  */
+  uint64_t fills;   /* fills so far                                        */
 } orc_cache;
+
+/* Replacement policies.  Sec. 3.4 leaves the policy to the user and Sec. 4.4 runs
+ * clock; FIFO is the textbook first-in first-out rule (the way filled earliest leaves
+ * first, whatever its use since). */
+enum { ORC_POLICY_CLOCK = 0, ORC_POLICY_FIFO = 1 };
 
 /* Set index of a page: the 64-bit golden-ratio multiplicative hash, whose upper 32
  * bits are reduced to [0, sets) by a multiply-shift.  Any number of sets works. */
@@ -89,12 +97,17 @@ orc_cache *orc_cache_new(uint32_t sets, uint32_t ways, uint64_t wb_cap) {
   c->data = (uint8_t *)calloc(n, ORC_PAGE);
   c->wb_cap = wb_cap;
   c->wb_log = (uint64_t *)calloc(wb_cap ? wb_cap : 1, sizeof(uint64_t));
+  c->filled = (uint64_t *)calloc(n, sizeof(uint64_t));
+  c->policy = ORC_POLICY_CLOCK;
   return c;
 }
+
+void orc_cache_set_policy(orc_cache *c, int policy) { c->policy = policy; }
 
 void orc_cache_free(orc_cache *c) {
   if (!c) return;
   free(c->page); free(c->state); free(c->ref); free(c->hand); free(c->data); free(c->wb_log);
+  free(c->filled);
   free(c);
 }
 
@@ -110,8 +123,9 @@ static void orc_log_wb(orc_cache *c, uint64_t page) {
  *   (b) otherwise the lowest INVALID way of the set is filled from the store;
  *   (d) otherwise the clock picks a victim: starting at the set's hand, a way whose
  *       reference bit is set has it cleared and the hand moves on; the first way with a
- *       clear bit is the victim and the hand moves past it.  A MODIFIED victim is written
- *       back to the store first.  The filled line gets its reference bit set.
+ *       clear bit is the victim and the hand moves past it (FIFO policy instead: the
+ *       way filled earliest is the victim).  A MODIFIED victim is written back to the
+ *       store first.  The filled line gets its reference bit set.
  * On return *way_out is the way now holding the page and the code says which case ran.
  * `store` is read on a fill and written on a write-back.
  */
@@ -134,7 +148,12 @@ int orc_cache_lookup(orc_cache *c, uint8_t *store, uint64_t page, uint32_t *way_
   for (uint32_t w = 0; w < c->ways; ++w) {
     if (c->state[base + w] == ORC_INVALID) { victim = w; break; }
   }
-  if (victim == c->ways) {
+  if (victim == c->ways && c->policy == ORC_POLICY_FIFO) {
+    /* FIFO: the way filled earliest */
+    victim = 0;
+    for (uint32_t w = 1; w < c->ways; ++w)
+      if (c->filled[base + w] < c->filled[base + victim]) victim = w;
+  } else if (victim == c->ways) {
     /* clock sweep: at most one full pass clears every bit, the next step finds a 0 */
     for (uint32_t step = 0; step < 2 * c->ways + 1; ++step) {
       uint32_t w = c->hand[s];
@@ -146,6 +165,8 @@ int orc_cache_lookup(orc_cache *c, uint8_t *store, uint64_t page, uint32_t *way_
         break;
       }
     }
+  }
+  if (c->state[base + victim] != ORC_INVALID) {
     uint64_t old = c->page[base + victim];
     if (victim_page) *victim_page = old;
     c->evictions++;
@@ -161,6 +182,7 @@ int orc_cache_lookup(orc_cache *c, uint8_t *store, uint64_t page, uint32_t *way_
   c->page[base + victim] = page;
   c->state[base + victim] = ORC_READY;
   c->ref[base + victim] = 1;
+  c->filled[base + victim] = ++c->fills;
   *way_out = victim;
   return code;
 }

@@ -30,6 +30,8 @@ AGILE_ASYNC = 1
 AGILE_FAULT_EIO = 1
 AGILE_FAULT_DROP_CQE = 2
 AGILE_TOKEN_HIT = (1 << 64) - 1
+AGILE_POLICY_CLOCK = 0
+AGILE_POLICY_FIFO = 1
 
 EXPORTED = [
     "agile_config_default", "agile_init", "agile_destroy", "agile_store_write",
@@ -40,7 +42,8 @@ EXPORTED = [
     "agile_serve_stop", "agile_serve_replay",
     "agile_cache_replay", "agile_cache_tags", "agile_cache_lines", "agile_cache_sets",
     "agile_stats", "agile_reset_stats", "agile_check", "agile_launch_shape", "agile_strerror",
-    "agile_config_parallelism",
+    "agile_config_parallelism", "agile_page_io", "agile_trace", "agile_link_probe", "agile_set_device_model",
+    "agile_bfs_hbm", "agile_spmv_hbm", "agile_device_view", "agile_run_reset",
 ]
 
 
@@ -62,6 +65,25 @@ class agile_config(C.Structure):
         ("max_ctas", C.c_uint32),
         ("prefetch_depth", C.c_uint32),
         ("app_warps", C.c_uint32),
+        ("trace_records", C.c_uint32),
+        ("num_devices", C.c_uint32),
+        ("cache_policy", C.c_uint32),
+        ("emu_device_read_gbps", C.c_double),
+        ("emu_device_write_gbps", C.c_double),
+    ]
+
+
+class agile_trace_rec(C.Structure):
+    _fields_ = [
+        ("page", C.c_uint64),
+        ("t_seen", C.c_uint64),
+        ("t_start", C.c_uint64),
+        ("t_done", C.c_uint64),
+        ("q", C.c_uint32),
+        ("cid", C.c_uint32),
+        ("opcode", C.c_uint32),
+        ("status", C.c_uint32),
+        ("pad", C.c_uint32 * 4),
     ]
 
 
@@ -143,6 +165,14 @@ def lib():
             "agile_serve_stop": (C.c_int, [vp]),
             "agile_serve_replay": (C.c_int, [vp, C.POINTER(agile_lookup_req), u32, vp, vp, u32, vp]),
             "agile_strerror": (C.c_char_p, [C.c_int]),
+            "agile_page_io": (C.c_int, [vp, u64, u64, vp, vp, vp]),
+            "agile_device_view": (C.c_int, [vp, vp, u64]),
+            "agile_run_reset": (C.c_int, [vp, vp]),
+            "agile_bfs_hbm": (C.c_int, [vp, vp, vp, u32, u64, i32, vp, vp, vp]),
+            "agile_spmv_hbm": (C.c_int, [vp, vp, vp, vp, u32, u32, u64, vp, vp, vp, vp]),
+            "agile_set_device_model": (C.c_int, [vp, u32, u32, C.c_double, C.c_double, C.c_double]),
+            "agile_trace": (C.c_int, [vp, vp, u32, C.POINTER(u32)]),
+            "agile_link_probe": (C.c_int, [vp, vp, u64, u32, u32, C.POINTER(C.c_double)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -247,6 +277,18 @@ def agile_spmv(ctx, offsets_byte0, cols_byte0, vals_byte0, n_rows, n_cols, d_x, 
                                 mode, stream), "agile_spmv")
 
 
+def agile_bfs_hbm(ctx, d_offsets, d_cols, n_vertices, n_cols, src, d_level, d_edges, stream) -> int:
+    """BFS over a CSR in device memory without the cache (Sec. 4.5 kernel time)."""
+    return _ok(lib().agile_bfs_hbm(ctx, d_offsets, d_cols, n_vertices, n_cols, src, d_level, d_edges, stream),
+               "agile_bfs_hbm")
+
+
+def agile_spmv_hbm(ctx, d_offsets, d_cols, d_vals, n_rows, n_cols, n_entries, d_x, d_y, d_entries, stream) -> int:
+    """SpMV over a CSR in device memory without the cache (Sec. 4.5 kernel time)."""
+    return _ok(lib().agile_spmv_hbm(ctx, d_offsets, d_cols, d_vals, n_rows, n_cols, n_entries, d_x, d_y, d_entries,
+                                    stream), "agile_spmv_hbm")
+
+
 def agile_bfs_noalloc(ctx, offsets_byte0, cols_byte0, n_vertices, n_cols, src, d_level, d_edges, mode,
                       stream) -> int:
     """BFS that allocates nothing during the call (scratch in a fixed device array)."""
@@ -326,6 +368,50 @@ def agile_launch_shape(ctx):
     a, b = C.c_uint32(), C.c_uint32()
     _ok(lib().agile_launch_shape(ctx, C.byref(a), C.byref(b)), "agile_launch_shape")
     return a.value, b.value
+
+
+def agile_set_device_model(ctx, num_devices=1, emu_latency_ns=0, emu_queue_gbps=0.0, emu_device_read_gbps=0.0,
+                           emu_device_write_gbps=0.0) -> int:
+    return _ok(lib().agile_set_device_model(ctx, num_devices, emu_latency_ns, emu_queue_gbps, emu_device_read_gbps,
+                                            emu_device_write_gbps), "agile_set_device_model")
+
+
+def agile_device_view(ctx, out_ptr, size) -> int:
+    """Copy the context's device view (for kernels built against agile_device.cuh)."""
+    return _ok(lib().agile_device_view(ctx, out_ptr, size), "agile_device_view")
+
+
+def agile_run_reset(ctx, stream) -> int:
+    return _ok(lib().agile_run_reset(ctx, stream), "agile_run_reset")
+
+
+def agile_page_io(ctx, page0: int, n: int):
+    """(reads, writes, dirtied) per store page page0 .. page0+n-1, as uint32 numpy arrays."""
+    import numpy as np
+    r = np.zeros(n, dtype=np.uint32)
+    w = np.zeros(n, dtype=np.uint32)
+    dt = np.zeros(n, dtype=np.uint32)
+    _ok(lib().agile_page_io(ctx, page0, n, r.ctypes.data, w.ctypes.data, dt.ctypes.data), "agile_page_io")
+    return r, w, dt
+
+
+TRACE_DTYPE = [("page", "<u8"), ("t_seen", "<u8"), ("t_start", "<u8"), ("t_done", "<u8"), ("q", "<u4"),
+               ("cid", "<u4"), ("opcode", "<u4"), ("status", "<u4"), ("pad", "<u4", (4,))]
+
+
+def agile_trace(ctx, cap: int):
+    """(records as a numpy structured array, number logged)."""
+    import numpy as np
+    out = np.zeros(cap, dtype=TRACE_DTYPE)
+    n = C.c_uint32()
+    _ok(lib().agile_trace(ctx, out.ctypes.data, cap, C.byref(n)), "agile_trace")
+    return out[:min(cap, n.value)], n.value
+
+
+def agile_link_probe(ctx, d_dst, nbytes, ctas=0, reps=3) -> float:
+    g = C.c_double()
+    _ok(lib().agile_link_probe(ctx, d_dst, nbytes, ctas, reps, C.byref(g)), "agile_link_probe")
+    return g.value
 
 
 def agile_strerror(code: int) -> str:

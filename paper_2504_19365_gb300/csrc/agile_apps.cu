@@ -52,18 +52,23 @@ struct EmbApp {
       }
     }
   }
-  // issue the pages of the next `cnt` rows of the stream from cursor c (advances c)
-  __device__ bool issue_rows(const Dev &d, const AppCtx &a, Cursor &c, uint32_t cnt) const {
+  // issue the pages of the next `cnt` rows of the stream from cursor c (advances c);
+  // rounds the backoff skips only advance the cursor
+  __device__ bool issue_rows(const Dev &d, const AppCtx &a, Cursor &c, uint32_t cnt, Backoff &bo) const {
     while (cnt && c.b < n_bags) {
       uint32_t take = (uint32_t)min((int64_t)cnt, c.e - c.i);
-      unsigned l = lane_id();
-      bool want = l < take;
-      uint64_t r = want ? (uint64_t)idx[c.i + l] : 0;
-      if (want && r >= rows) {
-        set_error(d, AGILE_EINVAL);
-        want = false;
+      if (bo.take()) {
+        unsigned l = lane_id();
+        bool want = l < take;
+        uint64_t r = want ? (uint64_t)idx[c.i + l] : 0;
+        if (want && r >= rows) {
+          set_error(d, AGILE_EINVAL);
+          want = false;
+        }
+        bool all_hit = false;
+        if (!warp_request(d, want, row_page(r), a.q0, false, a.deadline, nullptr, nullptr, &all_hit)) return false;
+        bo.result(all_hit);
       }
-      if (!warp_request(d, want, row_page(r), a.q0, false, a.deadline)) return false;
       c.i += take;
       cnt -= take;
       skip_empty(a, c);
@@ -130,7 +135,7 @@ struct EmbApp {
   }
 
   // general path for one bag: rows in groups, each group waiting for its pages as needed
-  __device__ bool slow_bag(const Dev &d, const AppCtx &a, uint32_t b, uint32_t nf4, Cursor &pf) const {
+  __device__ bool slow_bag(const Dev &d, const AppCtx &a, uint32_t b, uint32_t nf4, Cursor &pf, Backoff &bo) const {
     unsigned l = lane_id();
     const bool async = mode == AGILE_ASYNC;
     int64_t s = off[b], e = off[b + 1];
@@ -149,8 +154,11 @@ struct EmbApp {
       for (uint32_t g0 = 0; g0 < cnt; g0 += group) {
         uint32_t g1 = min(cnt, g0 + group);
         // keep the pages of the next `ahead` rows of the stream requested
-        if (async && !issue_rows(d, a, pf, g1 - g0)) return false;
-        if (!gather_sum<MF4>(d, a, g0, g1, page0 + byte / kPage, (uint32_t)(byte % kPage), nf4, acc)) return false;
+        if (async && !issue_rows(d, a, pf, g1 - g0, bo)) return false;
+        bool missed = false;
+        if (!gather_sum<MF4>(d, a, g0, g1, page0 + byte / kPage, (uint32_t)(byte % kPage), nf4, acc, &missed))
+          return false;
+        if (missed) bo.missed();
       }
     }
     store_out(b, acc, nf4);
@@ -163,7 +171,8 @@ struct EmbApp {
     const bool async = mode == AGILE_ASYNC;
     Cursor pf;  // prefetch cursor, `ahead` rows in front of the summation
     cur_init(a, pf);
-    if (async && !issue_rows(d, a, pf, ahead)) return;
+    Backoff bo;
+    if (async && !issue_rows(d, a, pf, ahead, bo)) return;
     constexpr int RB = MF4 >= 8 ? 1 : 8 / MF4;  // rows of an all-resident bag loaded before the next probe
     Prep cur;
     prep(d, a.warp, cur);
@@ -171,14 +180,15 @@ struct EmbApp {
       uint32_t nb = b + a.n_warps;
       if (!(cur.fast && cur.ok)) {
         // nothing pinned: the general path may wait
-        if (async && cur.fast && !issue_rows(d, a, pf, cur.cnt)) return;
-        if (!slow_bag(d, a, b, nf4, pf)) return;
+        if (async && cur.fast && !issue_rows(d, a, pf, cur.cnt, bo)) return;
+        if (async && cur.fast) bo.missed();  // a short bag not all resident
+        if (!slow_bag(d, a, b, nf4, pf, bo)) return;
         prep(d, nb, cur);
         continue;
       }
       // fast path: all pages of bag b are pinned.  Issue the first rows' loads, probe and
       // pin bag b+W while they are in flight, then add the rows in order.
-      if (async && !issue_rows(d, a, pf, cur.cnt)) return;
+      if (async && !issue_rows(d, a, pf, cur.cnt, bo)) return;
       float4 acc[MF4];
 #pragma unroll
       for (int k = 0; k < MF4; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -257,21 +267,28 @@ struct PipeApp {
     uint64_t u;
     uint32_t q;
   };
-  // request the pages of the next `cnt` rows of the stream from cursor c (advances c)
-  __device__ bool issue_ahead(const Dev &d, const AppCtx &a, Cursor &c, uint32_t cnt, uint64_t units) const {
+  // request the pages of the next `cnt` rows of the stream from cursor c (advances c);
+  // rounds the backoff skips only advance the cursor
+  __device__ bool issue_ahead(const Dev &d, const AppCtx &a, Cursor &c, uint32_t cnt, uint64_t units,
+                              Backoff &bo) const {
     const uint32_t per = n_tables * pooling;
     while (cnt && c.u < units) {
       uint32_t take = min(cnt, min(32u, per - c.q));
-      uint32_t q = c.q + lane_id();
-      bool want = lane_id() < take;
-      uint64_t t = c.u / n_bags, b = c.u % n_bags;
-      uint32_t k = want ? q / pooling : 0, p = want ? q % pooling : 0;
-      uint64_t r = want ? (uint64_t)idx[((t * n_tables + k) * n_bags + b) * pooling + p] : 0;
-      if (want && r >= rows) {
-        set_error(d, AGILE_EINVAL);
-        want = false;
+      if (bo.take()) {
+        uint32_t q = c.q + lane_id();
+        bool want = lane_id() < take;
+        uint64_t t = c.u / n_bags, b = c.u % n_bags;
+        uint32_t k = want ? q / pooling : 0, p = want ? q % pooling : 0;
+        uint64_t r = want ? (uint64_t)idx[((t * n_tables + k) * n_bags + b) * pooling + p] : 0;
+        if (want && r >= rows) {
+          set_error(d, AGILE_EINVAL);
+          want = false;
+        }
+        bool all_hit = false;
+        if (!warp_request(d, want, row_page(k, r), a.q0, false, a.deadline, nullptr, nullptr, &all_hit))
+          return false;
+        bo.result(all_hit);
       }
-      if (!warp_request(d, want, row_page(k, r), a.q0, false, a.deadline)) return false;
       c.q += take;
       cnt -= take;
       if (c.q == per) {
@@ -290,7 +307,8 @@ struct PipeApp {
     // async: the pages of the next `ahead` rows of the stream are requested before the
     // rows in front of them are gathered and computed on
     Cursor pf{a.warp, 0};
-    if (async && !issue_ahead(d, a, pf, ahead, units)) return;
+    Backoff bo;
+    if (async && !issue_ahead(d, a, pf, ahead, units, bo)) return;
     for (uint64_t u = a.warp; u < units; u += a.n_warps) {
       uint64_t t = u / n_bags, b = u % n_bags;
       float *o = out + u * (uint64_t)n_tables * dim;
@@ -309,8 +327,11 @@ struct PipeApp {
           uint64_t byte = (uint64_t)k * tstride + r * dim * 4;
           for (uint32_t g0 = 0; g0 < cnt; g0 += group) {
             uint32_t g1 = min(cnt, g0 + group);
-            if (async && !issue_ahead(d, a, pf, g1 - g0, units)) return;
-            if (!gather_sum<MF4>(d, a, g0, g1, page0 + byte / kPage, (uint32_t)(byte % kPage), nf4, acc)) return;
+            if (async && !issue_ahead(d, a, pf, g1 - g0, units, bo)) return;
+            bool missed = false;
+            if (!gather_sum<MF4>(d, a, g0, g1, page0 + byte / kPage, (uint32_t)(byte % kPage), nf4, acc, &missed))
+              return;
+            if (missed) bo.missed();
           }
         }
         // compute phase on this table's pooled row
@@ -355,15 +376,25 @@ struct PipeApp {
 // One slice (at most kSlice entries) of a long adjacency list, queued for any warp.
 struct HubEntry {
   long long p0, p1;          // column entries [p0, p1)
-  unsigned long long ready;  // (call epoch << 32) | (level + 1), written after p0, p1
-  unsigned long long pad;
+  unsigned long long ready;  // (launch epoch << 32) | (level + 1), written after p0, p1
+  unsigned long long aux;    // SpMV: row | first slice of the row << 32 | last << 33
+  unsigned long long carry;  // SpMV: (launch epoch << 32) | running sum after this slice
+  unsigned long long pad[3];
 };
+static_assert(sizeof(HubEntry) == 64, "one slice record per 64 bytes");
 
-// Every BFS call gets a fresh epoch, so an entry left by an earlier call or level can
-// never look published to a helper that reads it before its new owner has written it.
-static std::atomic<uint64_t> g_bfs_epoch{1};
+// A record is published with the number of the launch that wrote it (RunState::epoch,
+// drawn on the device for every launch) and the level, so a record left by an earlier
+// launch or level never looks published to a helper that reads it before its new owner
+// has written it.
+__device__ __forceinline__ uint64_t launch_epoch(const Dev &d) {
+  return ld_rlx64(&d.run->epoch) & 0xFFFFFFFFull;
+}
 
-struct BfsApp {
+// kDirect: the same kernel over a CSR held in device memory (h_off, h_col), without the
+// cache or the queues: the "kernel time" of the Sec. 4.5 three-step breakdown.
+template <bool kDirect>
+struct BfsAppT {
   uint64_t off_page0, col_page0;
   uint32_t n;
   int32_t *level;
@@ -371,12 +402,14 @@ struct BfsApp {
   uint32_t mode;
   HubEntry *hubq;
   uint32_t hub_cap;
-  uint64_t epoch;
   uint32_t *vis;  // visited bitmap: bit u set once level[u] is set (read through L1, may lag)
+  const uint8_t *h_off = nullptr, *h_col = nullptr;  // kDirect: the CSR arrays in HBM
 
   static constexpr uint32_t kChunk = 128;
 
-  __device__ __forceinline__ uint64_t tag(int32_t L) const { return (epoch << 32) | (uint32_t)(L + 1); }
+  __device__ __forceinline__ uint64_t tag(const Dev &d, int32_t L) const {
+    return (launch_epoch(d) << 32) | (uint32_t)(L + 1);
+  }
   static constexpr uint32_t kHub = 1024;
   static constexpr uint32_t kSlice = 2048;
 
@@ -401,6 +434,13 @@ struct BfsApp {
   template <typename T, int N>
   __device__ bool gather_n(const Dev &d, const AppCtx &a, uint64_t page0, const bool (&want)[N],
                            const uint64_t (&byte)[N], T (&val)[N], Pin &pc) const {
+    if constexpr (kDirect) {
+      const uint8_t *base = page0 == off_page0 ? h_off : h_col;
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (want[i]) val[i] = __ldg((const T *)(base + byte[i]));
+      return true;
+    }
     uint64_t pg[N];
     uint32_t in[N];
     bool todo[N];
@@ -499,7 +539,7 @@ struct BfsApp {
     uint32_t base = 0;
     if (l == 0) base = atomicAdd(&d.run->hub_count[L & 1], tot);
     base = __shfl_sync(kFull, base, 0);
-    const uint64_t t = tag(L);
+    const uint64_t t = tag(d, L);
     if ((uint64_t)base + tot > hub_cap) {
       for (uint64_t j = (uint64_t)base + l; j < hub_cap; j += 32) {
         hubq[j].p0 = hubq[j].p1 = 0;
@@ -583,7 +623,7 @@ struct BfsApp {
   // at the shared counters only now and then.
   __device__ bool help_hubs(const Dev &d, const AppCtx &a, int32_t L, uint32_t &found, Pin &pc) const {
     unsigned l = lane_id();
-    const uint64_t want_tag = tag(L);
+    const uint64_t want_tag = tag(d, L);
     const int par = L & 1;
     for (;;) {
       uint32_t k = 0;
@@ -620,7 +660,7 @@ struct BfsApp {
       p0 = __shfl_sync(kFull, p0, 0);
       p1 = __shfl_sync(kFull, p1, 0);
       if (p1 <= p0) continue;  // an empty record (a reservation past the queue's end)
-      if (mode == AGILE_ASYNC) {
+      if (!kDirect && mode == AGILE_ASYNC) {
         uint64_t q0p = col_page0 + ((uint64_t)p0 * 4) / kPage, q1p = col_page0 + ((uint64_t)(p1 - 1) * 4) / kPage;
         uint64_t pg = q0p + l;
         bool want = pg <= q1p && !(pc.valid && pc.page == pg);
@@ -689,6 +729,8 @@ struct BfsApp {
   }
 };
 
+using BfsApp = BfsAppT<false>;
+
 // ============================================================================ SpMV
 // y = A x over a CSR matrix on the store (Sec. 4.5 runs SpMV over the CSR graphs of its
 // BFS): int64 offsets, int32 columns and FP32 values are read through the cache; x and
@@ -701,14 +743,20 @@ struct BfsApp {
 // lanes (lane t adds its product to lane t-1's running sum), across steps through the
 // owner lane's running sum, so a row of fewer than kHub entries equals the sequential
 // definition bit for bit.  A row of at least kHub entries is queued as slices of
-// kSlice entries (the BFS slice queue); each slice is summed in order and added to y[v]
-// with an atomic add (y[v] = +0 is written before the slices are published), so such a
-// row is exact up to the order in which its slice sums arrive.
+// kSlice entries (the BFS slice queue), which any warp may take: the warp computes the
+// slice's products (into shared memory, all of its pages in flight together), then
+// takes the running sum the row's previous slice published (a slice waits for it
+// holding no pin) and adds its products to it in entry order, one add after the other;
+// the row's last slice writes y[v].  Every row is therefore the sequential definition
+// bit for bit; only the adds of a long row run one slice after the other.
 //   SYNC : every page when needed.
 //   ASYNC: while the warp computes unit i, the offsets of unit i+1 are read and the
 //          column and value pages of its entries are requested, and the offsets pages
 //          of unit i+2 are requested.
-struct SpmvApp {
+// kDirect: the same kernel over a CSR held in device memory (h_off, h_col, h_val),
+// without the cache or the queues (Sec. 4.5 "kernel time").
+template <bool kDirect>
+struct SpmvAppT {
   uint64_t off_page0, col_page0, val_page0;
   uint32_t n;    // rows
   const float *x;
@@ -718,11 +766,11 @@ struct SpmvApp {
   uint32_t mode;
   HubEntry *hubq;
   uint32_t hub_cap;
-  uint64_t epoch;
+  const uint8_t *h_off = nullptr, *h_col = nullptr, *h_val = nullptr;  // kDirect: the CSR in HBM
 
   static constexpr uint32_t kChunk = 128;
   static constexpr uint32_t kHub = 1024;
-  static constexpr uint32_t kSlice = 2048;
+  static constexpr uint32_t kSlice = 1024;  // = the products buffer of a warp
 
   struct Pin {
     uint64_t page;
@@ -744,6 +792,13 @@ struct SpmvApp {
   template <typename T, int N>
   __device__ bool gather(const Dev &d, const AppCtx &a, uint64_t page0, const bool (&want)[N],
                          const uint64_t (&byte)[N], T (&val)[N], Pin &pc, Pin &o1, Pin &o2) const {
+    if constexpr (kDirect) {
+      const uint8_t *base = page0 == off_page0 ? h_off : (page0 == col_page0 ? h_col : h_val);
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (want[i]) val[i] = __ldg((const T *)(base + byte[i]));
+      return true;
+    }
     uint64_t pg[N];
     uint32_t in[N];
     bool todo[N];
@@ -838,8 +893,8 @@ struct SpmvApp {
     return true;
   }
 
-  // queue the lanes' rows of at least kHub entries as slices (as the BFS does); a lane
-  // whose row is queued writes y[v] = +0 before its slices are published
+  // queue the lanes' rows of at least kHub entries as slices (as the BFS does); each
+  // record names its row and whether it is the row's first and last slice
   __device__ bool push_hub(const Dev &d, uint32_t v, uint32_t deg, int64_t s, int64_t e) const {
     unsigned l = lane_id();
     bool hub = deg >= kHub;
@@ -857,7 +912,7 @@ struct SpmvApp {
     uint32_t base = 0;
     if (l == 0) base = atomicAdd(&d.run->hub_count[0], tot);
     base = __shfl_sync(kFull, base, 0);
-    const uint64_t t = (epoch << 32) | 1u;
+    const uint64_t t = (launch_epoch(d) << 32) | 1u;
     if ((uint64_t)base + tot > hub_cap) {
       for (uint64_t j = (uint64_t)base + l; j < hub_cap; j += 32) {
         hubq[j].p0 = hubq[j].p1 = 0;
@@ -865,8 +920,6 @@ struct SpmvApp {
       }
       return false;  // summed here
     }
-    if (hub) y[v] = 0.0f;
-    __syncwarp();
     for (unsigned m = hm; m; m &= m - 1) {
       int h = __ffs(m) - 1;
       int64_t sh = __shfl_sync(kFull, s, h), eh = __shfl_sync(kFull, e, h);
@@ -877,8 +930,7 @@ struct SpmvApp {
         int64_t p0 = sh + (int64_t)j * kSlice;
         r->p0 = p0;
         r->p1 = min(eh, p0 + (int64_t)kSlice);
-        r->pad = vh;
-        __threadfence();  // y[v] = 0 (written by another lane) before the record is seen
+        r->aux = (uint64_t)vh | ((uint64_t)(j == 0) << 32) | ((uint64_t)(j + 1 == nh) << 33);
         st_rel64(&r->ready, t);
       }
     }
@@ -945,6 +997,7 @@ struct SpmvApp {
 
   // stage A: request the offsets pages of a unit (its offsets [v0, min(v0+32, n)])
   __device__ bool stage_a(const Dev &d, const AppCtx &a, uint32_t v0) const {
+    if constexpr (kDirect) return true;
     uint32_t vend = min(v0 + 32, n);
     uint64_t pa = off_page0 + ((uint64_t)v0 * 8) / kPage, pb = off_page0 + ((uint64_t)vend * 8) / kPage;
     bool want = (lane_id() == 0) || (lane_id() == 1 && pb != pa);
@@ -972,7 +1025,7 @@ struct SpmvApp {
       lo = min(lo, __shfl_xor_sync(kFull, lo, o));
       hi = max(hi, __shfl_xor_sync(kFull, hi, o));
     }
-    if (hi <= lo) return true;
+    if (kDirect || hi <= lo) return true;
     uint64_t c0 = ((uint64_t)lo * 4) / kPage, c1 = ((uint64_t)(hi - 1) * 4) / kPage;
     bool want = c0 + lane_id() <= c1;
     if (!warp_request_call(d, want, col_page0 + c0 + lane_id(), a.q0, false, a.deadline)) return false;
@@ -981,8 +1034,11 @@ struct SpmvApp {
 
   // take queued slices until every slice is taken (the BFS slice queue, one level)
   __device__ bool help_hubs(const Dev &d, const AppCtx &a, Pin &po, Pin &pcol, Pin &pval) const {
+    __shared__ float prod_buf[kWarps][kSlice];  // products of the slice a warp holds
+    float *buf = prod_buf[threadIdx.x >> 5];
     unsigned l = lane_id();
-    const uint64_t want_tag = (epoch << 32) | 1u;
+    const uint64_t ep = launch_epoch(d);
+    const uint64_t want_tag = (ep << 32) | 1u;
     for (;;) {
       uint32_t k = 0;
       if (l == 0) k = atomicAdd(&d.run->hub_cursor[0], 1u);
@@ -1013,34 +1069,78 @@ struct SpmvApp {
       }
       if (state == 2) return true;
       int64_t p0 = 0, p1 = 0;
-      uint32_t row = 0;
+      uint64_t aux = 0;
       if (l == 0) {
         p0 = ld_cg_s64(&r->p0);
         p1 = ld_cg_s64(&r->p1);
-        row = (uint32_t)ld_cg_s64(&r->pad);
+        aux = (uint64_t)ld_cg_s64(&r->aux);
       }
       p0 = __shfl_sync(kFull, p0, 0);
       p1 = __shfl_sync(kFull, p1, 0);
-      row = __shfl_sync(kFull, row, 0);
+      aux = __shfl_sync(kFull, aux, 0);
       if (p1 <= p0) continue;  // an empty record (a reservation past the queue's end)
+      const uint32_t row = (uint32_t)aux;
+      const bool first = (aux >> 32) & 1, last = (aux >> 33) & 1;
       release(d, po);
-      if (mode == AGILE_ASYNC) {
+      if (!kDirect && mode == AGILE_ASYNC) {
         uint64_t c0 = ((uint64_t)p0 * 4) / kPage, c1 = ((uint64_t)(p1 - 1) * 4) / kPage;
         bool want = c0 + l <= c1;
         if (!warp_request_call(d, want, col_page0 + c0 + l, a.q0, false, a.deadline)) return false;
         if (!warp_request_call(d, want, val_page0 + c0 + l, a.q0, false, a.deadline)) return false;
       }
-      float sum = 0.0f;  // the slice's running sum (the same in every lane)
-      for (int64_t b0 = p0; b0 < p1; b0 += 32) {
-        int64_t pos = b0 + l;
-        bool act = pos < p1;
-        float prod = 0.f;
-        if (!product(d, a, act, act ? (uint64_t)pos : (uint64_t)p0, prod, po, pcol, pval)) return false;
-        float run = (l == 0) ? __fadd_rn(sum, prod) : prod;
-        run = chain(run, prod, act && l != 0);
-        sum = __shfl_sync(kFull, run, (int)min((int64_t)31, p1 - 1 - b0));
+      // products of the slice, two entries a lane at a time, into the warp's buffer
+      for (int64_t b0 = p0; b0 < p1; b0 += 64) {
+        bool on[2];
+        uint64_t byte[2];
+        int32_t col[2] = {0, 0};
+        float val[2] = {0.f, 0.f};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          int64_t pos = b0 + 32 * h + l;
+          on[h] = pos < p1;
+          byte[h] = (uint64_t)(on[h] ? pos : p0) * 4;
+        }
+        if (!gather<int32_t, 2>(d, a, col_page0, on, byte, col, pcol, pval, po)) return false;
+        if (!gather<float, 2>(d, a, val_page0, on, byte, val, pval, pcol, po)) return false;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (on[h]) {
+            float xv = 0.f;
+            if ((uint32_t)col[h] < n_x) xv = __ldg(&x[col[h]]);
+            else set_error(d, AGILE_EINVAL);
+            buf[b0 - p0 + 32 * h + l] = __fmul_rn(val[h], xv);
+          }
+        }
       }
-      if (l == 0) atomicAdd(&y[row], sum);
+      // the running sum of the row so far: +0 before its first entry, else what the
+      // previous slice (the record before this one) published; waited for holding no pin
+      float run = 0.0f;
+      if (!first) {
+        release(d, pcol);
+        release(d, pval);
+        const HubEntry *prev = &hubq[k - 1];
+        uint64_t cw = 0;
+        uint32_t ns2 = 32;
+        for (;;) {
+          if (l == 0) cw = ld_acq64(&prev->carry);
+          cw = __shfl_sync(kFull, cw, 0);
+          if ((cw >> 32) == ep) break;
+          if (gtimer() > a.deadline || aborted(d)) {
+            if (l == 0) set_error(d, -110);
+            return false;
+          }
+          backoff(ns2, 256);
+        }
+        run = __uint_as_float((uint32_t)cw);
+      }
+      __syncwarp();
+      if (l == 0) {
+        const uint32_t cnt = (uint32_t)(p1 - p0);
+        for (uint32_t i = 0; i < cnt; ++i) run = __fadd_rn(run, buf[i]);
+        if (last) y[row] = run;
+        else st_rel64(&r->carry, (ep << 32) | __float_as_uint(run));
+      }
+      __syncwarp();
     }
   }
 
@@ -1051,7 +1151,7 @@ struct SpmvApp {
     Pin po{0, 0, false}, pcol{0, 0, false}, pval{0, 0, false};
     bool ok = true;
     uint32_t chunk = 0, sub = kChunk;
-    if (mode == AGILE_ASYNC) {
+    if (!kDirect && mode == AGILE_ASYNC) {
       uint32_t u0 = 0, v1 = 0, v2 = 0;
       int64_t s0 = 0, s1 = 0;
       uint32_t dg0 = 0, dg1 = 0;
@@ -1101,6 +1201,8 @@ struct SpmvApp {
   }
 };
 
+using SpmvApp = SpmvAppT<false>;
+
 __global__ void bfs_init_kernel(int32_t *level, uint32_t *vis, uint32_t n, int32_t src) {
   uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (i < n) level[i] = (i == (uint64_t)src) ? 0 : -1;
@@ -1126,33 +1228,42 @@ int bfs_check(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_
 
 int bfs_launch(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_t n_vertices, int32_t src,
                int32_t *d_level, uint64_t *d_edges_scanned, uint32_t mode, void *stream, HubEntry *hubq,
-               uint32_t hub_cap, uint32_t *vis) {
+               uint32_t hub_cap, uint32_t *vis, const int64_t *h_off = nullptr, const int32_t *h_col = nullptr) {
   cudaStream_t s = as_stream(stream);
   bfs_init_kernel<<<(n_vertices + 255) / 256, 256, 0, s>>>(d_level, vis, n_vertices, src);
   AGILE_CUDA_TRY(cudaGetLastError());
   if (d_edges_scanned) AGILE_CUDA_TRY(cudaMemsetAsync(d_edges_scanned, 0, 8, s));
+  if (h_off) {
+    // the CSR in HBM: offsets and columns are told apart by their (distinct) page
+    // numbers 0 and 1 only
+    BfsAppT<true> app{0, 1, n_vertices, d_level, (unsigned long long *)d_edges_scanned, AGILE_SYNC, hubq,
+                      hub_cap, vis, (const uint8_t *)h_off, (const uint8_t *)h_col};
+    return launch_engine(c, app, stream, warps_for_cache(c, 2, 32));
+  }
   BfsApp app{offsets_byte0 / kPage, cols_byte0 / kPage, n_vertices, d_level,
-             (unsigned long long *)d_edges_scanned, mode, hubq, hub_cap,
-             g_bfs_epoch.fetch_add(1) & 0xFFFFFFFFull, vis};
+             (unsigned long long *)d_edges_scanned, mode, hubq, hub_cap, vis};
   // about two lines per warp (one pinned, one being filled; a slice's requested pages are
   // scanned right away)
   return launch_engine(c, app, stream, warps_for_cache(c, 2, 32));
 }
 
 // ---------------------------------------------------------------- BFS without allocation
-// Some callers cannot call cudaMalloc when they run a BFS: code recorded into a CUDA
-// graph or running under stream capture (allocation is not allowed there), and
-// latency-critical loops in which an allocation's implicit device synchronisation
-// would stall every other stream.  For them agile_bfs_noalloc keeps the long-list
-// queue, the only scratch the BFS kernel needs beyond the context, in this fixed
-// device array, and the visited bitmap in a second one.  Every GPU that loads the
-// library holds them (1 MiB + 4 MiB) until the process exits.  Host code must not pass the array's name to a kernel: on the host it is a
-// stand-in symbol, not a device address, so its address is fetched once per device with
-// cudaGetSymbolAddress, with that device current, on the first call on that device.
+// Some callers cannot call cudaMalloc when they run a BFS: code running under stream
+// capture (allocation is not allowed there), and latency-critical loops in which an
+// allocation's implicit device synchronisation would stall every other stream.  For
+// them agile_bfs_noalloc keeps the long-list queue, the only scratch the BFS kernel
+// needs beyond the context, in this fixed device array, and the visited bitmap in a
+// second one.  Every GPU that loads the library holds them (2 MiB + 4 MiB) until the
+// process exits.  Host code must not pass the array's name to a kernel: on the host it
+// is a stand-in symbol, not a device address, so its address is fetched once per device
+// with cudaGetSymbolAddress, with that device current, on the first call on that device
+// (and kept for the process: a device reset between calls is not supported).
 // No queue entry needs clearing between calls: an entry is written before it is
-// published, and publication carries the call's epoch, so what an earlier call left
-// behind is never taken for a live entry; the bitmap is cleared by every call.  All calls on one device share the array, so calls of this
-// entry point that overlap on that GPU (from any context or stream) race on it.
+// published, and publication carries the number the device gave the launch (one per
+// kernel execution, not per host call), so what an earlier launch left behind is never
+// taken for a live entry; the bitmap is cleared by every call.  All calls on one device
+// share the arrays, so calls of this entry point that overlap on that GPU (from any
+// context or stream) race on them.
 constexpr uint32_t kNoAllocHubMax = 32768;
 constexpr uint32_t kNoAllocVisWords = 1u << 20;  // vertices up to 2^25
 static __device__ __align__(256) HubEntry g_bfs_hub_scratch[kNoAllocHubMax];
@@ -1180,10 +1291,17 @@ int noalloc_scratch(int device, HubEntry **out, uint32_t **vis_out) {
   return AGILE_OK;
 }
 
-// Slice queue of a CSR walk (BFS, SpMV): a level has at most (column entries) / kHub
-// slices, so the entries the store can hold beyond cols_byte0 bound it.
-int ensure_slice_queue(agile_ctx *c, uint64_t cols_byte0) {
-  uint64_t cap = (c->cfg.store_bytes - cols_byte0) / 4 / BfsApp::kHub + 1;
+// Slice queue of a CSR walk (BFS, SpMV).  A list of d >= kHub entries takes
+// ceil(d / kSlice) records: at most d / 1024 for the BFS (kSlice = 2048 = 2 kHub), at
+// most 2 d / 1024 for the SpMV (kSlice = kHub); the entries the store can hold beyond
+// cols_byte0 bound d.  `per_1024`: records per 1024 entries.
+int ensure_slice_entries(agile_ctx *c, uint64_t entries, uint32_t per_1024);
+int ensure_slice_queue(agile_ctx *c, uint64_t cols_byte0, uint32_t per_1024 = 1) {
+  return ensure_slice_entries(c, (c->cfg.store_bytes - cols_byte0) / 4, per_1024);
+}
+// ... the same for a list of `entries` column entries
+int ensure_slice_entries(agile_ctx *c, uint64_t entries, uint32_t per_1024) {
+  uint64_t cap = entries / 1024 * per_1024 + 1;
   if (cap > (1u << 22)) cap = 1u << 22;
   if (cap < 1024) cap = 1024;
   if (!c->bfs_hubq || c->bfs_hub_cap < cap) {
@@ -1310,6 +1428,40 @@ int agile_bfs_noalloc(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0,
                     scratch, kNoAllocHubMax, vis);
 }
 
+int agile_bfs_hbm(agile_ctx *c, const int64_t *d_offsets, const int32_t *d_cols, uint32_t n_vertices,
+                  uint64_t n_cols, int32_t src, int32_t *d_level, uint64_t *d_edges_scanned, void *stream) {
+  if (!c || !d_offsets || !d_cols || !d_level) return AGILE_EINVAL;
+  if (n_vertices == 0 || src < 0 || (uint32_t)src >= n_vertices) return AGILE_EINVAL;
+  AGILE_CUDA_TRY(cudaSetDevice(c->device));
+  int r = ensure_slice_entries(c, n_cols, 1);
+  if (r) return r;
+  uint64_t words = ((uint64_t)n_vertices + 31) / 32;
+  if (!c->bfs_vis || c->bfs_vis_words < words) {
+    if (c->bfs_vis) cudaFree(c->bfs_vis);
+    c->bfs_vis = nullptr;
+    AGILE_CUDA_TRY(cudaMalloc(&c->bfs_vis, words * 4));
+    c->bfs_vis_words = words;
+  }
+  return bfs_launch(c, 0, 0, n_vertices, src, d_level, d_edges_scanned, AGILE_SYNC, stream,
+                    (HubEntry *)c->bfs_hubq, c->bfs_hub_cap, (uint32_t *)c->bfs_vis, d_offsets, d_cols);
+}
+
+int agile_spmv_hbm(agile_ctx *c, const int64_t *d_offsets, const int32_t *d_cols, const float *d_vals,
+                   uint32_t n_rows, uint32_t n_cols, uint64_t n_entries, const float *d_x, float *d_y,
+                   uint64_t *d_entries, void *stream) {
+  if (!c) return AGILE_EINVAL;
+  if (n_rows == 0) return AGILE_OK;
+  if (!d_offsets || !d_cols || !d_vals || !d_x || !d_y) return AGILE_EINVAL;
+  AGILE_CUDA_TRY(cudaSetDevice(c->device));
+  int r = ensure_slice_entries(c, n_entries, 2);
+  if (r) return r;
+  if (d_entries) AGILE_CUDA_TRY(cudaMemsetAsync(d_entries, 0, 8, as_stream(stream)));
+  SpmvAppT<true> app{0, 1, 2, n_rows, d_x, n_cols, d_y, (unsigned long long *)d_entries, AGILE_SYNC,
+                     (HubEntry *)c->bfs_hubq, c->bfs_hub_cap, (const uint8_t *)d_offsets, (const uint8_t *)d_cols,
+                     (const uint8_t *)d_vals};
+  return launch_engine(c, app, stream, warps_for_cache(c, 3, 32));
+}
+
 int agile_spmv(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint64_t vals_byte0, uint32_t n_rows,
                uint32_t n_cols, const float *d_x, float *d_y, uint64_t *d_entries, uint32_t mode, void *stream) {
   if (!c || mode > 1) return AGILE_EINVAL;
@@ -1319,12 +1471,11 @@ int agile_spmv(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint64
   if (offsets_byte0 + ((uint64_t)n_rows + 1) * 8 > c->cfg.store_bytes) return AGILE_EINVAL;
   if (cols_byte0 >= c->cfg.store_bytes || vals_byte0 >= c->cfg.store_bytes) return AGILE_EINVAL;
   AGILE_CUDA_TRY(cudaSetDevice(c->device));
-  int r = ensure_slice_queue(c, std::min(cols_byte0, vals_byte0));
+  int r = ensure_slice_queue(c, std::min(cols_byte0, vals_byte0), 2);
   if (r) return r;
   if (d_entries) AGILE_CUDA_TRY(cudaMemsetAsync(d_entries, 0, 8, as_stream(stream)));
   SpmvApp app{offsets_byte0 / kPage, cols_byte0 / kPage, vals_byte0 / kPage, n_rows, d_x, n_cols, d_y,
-              (unsigned long long *)d_entries, mode, (HubEntry *)c->bfs_hubq, c->bfs_hub_cap,
-              g_bfs_epoch.fetch_add(1) & 0xFFFFFFFFull};
+              (unsigned long long *)d_entries, mode, (HubEntry *)c->bfs_hubq, c->bfs_hub_cap};
   // each warp pins one page of each of three arrays and requests up to two units ahead
   return launch_engine(c, app, stream, warps_for_cache(c, mode == AGILE_ASYNC ? 6 : 3, 32));
 }

@@ -72,6 +72,20 @@ uint32_t running_app_warps(agile_ctx *c, uint32_t active) {
   return (uint32_t)std::max<uint64_t>(1, want && want < n_app ? want : n_app);
 }
 
+// Launches of this translation unit on the current device, counted on the device, so
+// that a launch replayed from a recorded stream still gets a number of its own.
+static __device__ unsigned long long g_launch_seq;
+
+// Zero the per-launch state and give the launch its number (RunState::epoch).  Runs on
+// the call's stream right before the engine kernel.
+static __global__ void run_reset_kernel(RunState *r) {
+  static_assert(sizeof(RunState) % 4 == 0, "RunState is cleared in 4-byte words");
+  uint32_t *w = (uint32_t *)r;
+  for (uint32_t i = threadIdx.x; i < sizeof(RunState) / 4; i += blockDim.x) w[i] = 0u;
+  __syncthreads();
+  if (threadIdx.x == 0) r->epoch = atomicAdd(&g_launch_seq, 1ull) + 1ull;
+}
+
 // `active`: application warps the call wants (0 = every app warp of the grid); the
 // context's app_warps setting overrides it.
 template <class App>
@@ -80,7 +94,8 @@ int launch_engine(agile_ctx *c, const App &app, void *stream, uint32_t active = 
   AGILE_CUDA_TRY(cudaSetDevice(c->device));
   int grid = engine_grid<App>(c);
   if (grid <= 0) return AGILE_ECUDA;
-  AGILE_CUDA_TRY(cudaMemsetAsync(c->dev.run, 0, sizeof(RunState), s));
+  run_reset_kernel<<<1, 128, 0, s>>>(c->dev.run);
+  AGILE_CUDA_TRY(cudaGetLastError());
   Dev d = c->dev;
   d.app_active = c->cfg.app_warps ? c->cfg.app_warps : active;
   App a = app;

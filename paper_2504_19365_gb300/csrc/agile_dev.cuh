@@ -41,6 +41,9 @@ __host__ __device__ __forceinline__ uint64_t tag_make(uint64_t page, uint64_t st
   return (page << PAGE_SHIFT) | (ref ? TAG_REF : 0) | st;
 }
 
+// replacement policies (agile.h AGILE_POLICY_*)
+constexpr uint32_t kPolicyClock = 0, kPolicyFifo = 1;
+
 // ---------------------------------------------------------------- queues (Sec. 3.3.1)
 constexpr uint64_t SQE_EMPTY = 0, SQE_UPDATED = 1, SQE_ISSUED = 2;
 constexpr uint32_t OP_FLUSH = 0x00, OP_WRITE = 0x01, OP_READ = 0x02;
@@ -61,7 +64,7 @@ enum Stat {
   S_BYTES_READ, S_BYTES_WRITTEN, S_PREFETCHES, S_TIMEOUTS, S_COUNT
 };
 
-// per-launch state, zeroed before every launch
+// per-launch state, zeroed before every launch (and numbered) by run_reset_kernel
 struct RunState {
   uint32_t app_done;      // app warps finished
   uint32_t error;         // first error code (negated AGILE_E*), 0 = none
@@ -70,10 +73,22 @@ struct RunState {
   uint32_t work[4];       // dynamic work counters
   unsigned long long acc[4];  // accumulators (edges scanned, discovered vertices, ...)
   uint32_t flag[4];
+  unsigned long long epoch;  // number of this launch among the device's launches (never 0)
   // BFS slice queue, per level parity, each on a line of its own (hot words)
   alignas(128) uint32_t hub_count[2];  // slices of long adjacency lists reserved
   alignas(128) uint32_t hub_cursor[2];  // next slice ticket
   alignas(128) uint32_t units_done[2];  // warps that finished their own vertices
+};
+
+// One command as the emulated device served it (times from %globaltimer, ns).
+struct TraceRec {
+  unsigned long long page;    // store page of the command
+  unsigned long long t_seen;  // doorbell that exposed it first read by the device (0 when
+                              // the device runs without a latency or throughput model)
+  unsigned long long t_start; // taken by an engine: data movement starts
+  unsigned long long t_done;  // completion entry posted
+  uint32_t q, cid, opcode, status;
+  uint32_t pad[4];
 };
 
 struct Dev {
@@ -103,8 +118,23 @@ struct Dev {
   unsigned long long *emu_busy;     // [Q] ns at which the queue's device pipe is free
   unsigned long long *emu_arrival;  // [Q*depth] ns at which the device saw the command
   uint8_t *staging;
+  // per store page: reads and writes the device served, dirty epochs the cache opened
+  // (a clean line turned MODIFIED, or a write-through issued); every dirty epoch ends in
+  // exactly one write
+  uint32_t *pg_reads, *pg_writes, *pg_dirty;
+  // command trace (optional): one record per command the device served
+  struct TraceRec *trace;
+  uint32_t trace_cap;
+  uint32_t *trace_n;
+  // backing devices: page p lives on device p mod ndev at block p / ndev; queue q
+  // belongs to device q mod ndev (Sec. 4.3: requests interleaved over the SSDs)
+  uint32_t ndev;
+  // replacement policy of the cache (AGILE_POLICY_*)
+  uint32_t policy;
   // emulated device model
   uint64_t lat_ns, ns_per_page;
+  uint64_t ns_rd_dev, ns_wr_dev;    // per-device time of one page read / written (0 = no cap)
+  unsigned long long *dev_busy;     // [ndev] ns up to which the device is booked
   uint32_t fault_flags, fault_thresh;
   uint64_t seed;
   // run
@@ -208,6 +238,12 @@ __device__ __forceinline__ void stat_warp(const Dev &d, int s, uint32_t v) {
   if (lane_id() == 0) atomicAdd(stat_ptr(d, s), (unsigned long long)sum);
 }
 
+// A cache line of `page` turned from clean to MODIFIED (or a write-through was issued):
+// the page owes the store one write.
+__device__ __forceinline__ void note_dirty(const Dev &d, uint64_t page) {
+  atomicAdd(&d.pg_dirty[page], 1u);
+}
+
 // record the first error of the launch and of the context
 __device__ __forceinline__ void set_error(const Dev &d, int code) {
   atomicCAS(&d.run->error, 0u, (uint32_t)(-code));
@@ -285,13 +321,26 @@ __device__ __forceinline__ bool sq_try_reserve(const Dev &d, uint32_t q, uint32_
   return false;
 }
 
-// SQ selection (Sec. 3.3.1): start at the thread's own queue, on a full queue try the
-// next one; false after one pass over every queue.
-__device__ __forceinline__ bool sq_reserve_any(const Dev &d, uint32_t q0, uint32_t n, uint32_t &q,
+// Backing device of a store page and its block number there (4 KiB blocks).
+__host__ __device__ __forceinline__ uint32_t dev_of_page(const Dev &d, uint64_t page) {
+  return d.ndev > 1 ? (uint32_t)(page % d.ndev) : 0u;
+}
+__host__ __device__ __forceinline__ uint64_t block_of_page(const Dev &d, uint64_t page) {
+  return d.ndev > 1 ? page / d.ndev : page;
+}
+
+// SQ selection (Sec. 3.3.1): among the queues of the page's device, start at the one
+// nearest the thread's own queue, on a full queue try the device's next one; false
+// after one pass over them.
+__device__ __forceinline__ bool sq_reserve_dev(const Dev &d, uint32_t q0, uint32_t dv, uint32_t n, uint32_t &q,
                                                uint32_t &slot, uint32_t &ticket) {
-  for (uint32_t k = 0; k < d.Q; ++k) {
-    uint32_t qq = q0 + k;
-    if (qq >= d.Q) qq -= d.Q;
+  const uint32_t nd = d.ndev > 1 ? d.ndev : 1u;
+  const uint32_t per = d.Q / nd;  // queues of one device
+  uint32_t k0 = (q0 / nd) % per;
+  for (uint32_t k = 0; k < per; ++k) {
+    uint32_t kk = k0 + k;
+    if (kk >= per) kk -= per;
+    uint32_t qq = kk * nd + dv;
     if (sq_try_reserve(d, qq, n, slot, ticket)) {
       q = qq;
       return true;
@@ -308,7 +357,7 @@ __device__ __forceinline__ void sq_commit(const Dev &d, uint32_t q, uint32_t slo
                                           uint64_t ctx) {
   uint64_t i = (uint64_t)q * d.depth + slot;
   uint32_t *e = d.sq[i].dw;
-  uint64_t slba = page * (kPage / 512);
+  uint64_t slba = block_of_page(d, page) * (kPage / 512);
   int4 a = make_int4((int)(opcode | (slot << 16)), 1, 0, 0);                      // dw0-3
   int4 b = make_int4(0, 0, (int)(uint32_t)prp1, (int)(uint32_t)(prp1 >> 32));      // dw4-7
   int4 c = make_int4(0, 0, (int)(uint32_t)slba, (int)(uint32_t)(slba >> 32));      // dw8-11
@@ -414,7 +463,8 @@ __device__ __forceinline__ int64_t sh_insert(const Dev &d, uint64_t page, uint64
       st_rel64(&d.sh_key[base + free_k], 0ull);
       return -1;
     }
-    st_rlx64(&d.sh_val[base + free_k], kind);
+    (void)kind;
+    st_rlx64(&d.sh_val[base + free_k], 0ull);  // the token of the read, once issued
     return (int64_t)(base + free_k);
   }
   return -2;
@@ -422,6 +472,20 @@ __device__ __forceinline__ int64_t sh_insert(const Dev &d, uint64_t page, uint64
 __device__ __forceinline__ void sh_remove(const Dev &d, uint64_t slot) {
   st_rlx64(&d.sh_val[slot], 0ull);
   st_rel64(&d.sh_key[slot], 0ull);
+}
+// Token of the read in flight for `page`, 0 when there is none (or it is not published
+// yet).  The key is read again after the value: an entry removed (and maybe reused)
+// meanwhile is not taken; one re-inserted for the same page carries a token of the same
+// page, which is as good.
+__device__ __forceinline__ uint64_t sh_token(const Dev &d, uint64_t page) {
+  uint64_t key = page + 1;
+  uint64_t base = (uint64_t)sh_bucket(d, page) * 4;
+  for (int k = 0; k < 4; ++k) {
+    if (ld_acq64(&d.sh_key[base + k]) != key) continue;
+    uint64_t v = ld_acq64(&d.sh_val[base + k]);
+    if (v && ld_acq64(&d.sh_key[base + k]) == key) return v;
+  }
+  return 0;
 }
 
 // ================================================================ cache (Sec. 3.4)
@@ -480,10 +544,13 @@ __device__ __forceinline__ void cache_unclaim(const Dev &d, uint32_t line, uint6
   }
 }
 
-enum Miss { M_ISSUED = 0, M_HIT = 1, M_BUSY = 2, M_RETRY = 3 };
+// M_RETRY_RING: as M_RETRY, but a no-op command was committed to (q, slot, ticket) and
+// must be rung.
+enum Miss { M_ISSUED = 0, M_HIT = 1, M_BUSY = 2, M_RETRY = 3, M_RETRY_RING = 4 };
 
 struct Issued {
-  uint32_t q, slot, ticket;
+  uint32_t q, slot, ticket;     // the command to ring (the read, when there is one)
+  uint32_t q2, slot2, ticket2;  // a second command on another queue (q2 = ~0: none)
   int code;  // 1 fill, 2 evict READY, 3 write-back MODIFIED
 };
 
@@ -534,7 +601,7 @@ static __device__ int cache_miss(const Dev &d, uint64_t page, uint32_t q0, uint3
       continue;
     }
     if (st == ST_BUSY || (t & (PIN_MASK | TAG_WB))) continue;
-    if (t & TAG_REF) {
+    if ((t & TAG_REF) && d.policy == kPolicyClock) {
       atomicAnd(&d.tag[base + w], ~TAG_REF);
       continue;
     }
@@ -557,17 +624,38 @@ static __device__ int cache_miss(const Dev &d, uint64_t page, uint32_t q0, uint3
   }
   line = (uint32_t)(base + victim);
   bool wb = tag_state(old) == ST_MODIFIED;
+  // Queue slots: the write-back and the read go to the queues of their pages' devices.
+  // On one device they take two consecutive slots of one queue, reserved together; on
+  // two devices the write-back's slot is reserved first, and if the read then finds no
+  // slot the write-back slot is spent on a no-op command (a slot once reserved must be
+  // committed) and the miss is retried holding nothing.
+  const uint32_t dv_fill = dev_of_page(d, page);
+  const uint32_t dv_wb = wb ? dev_of_page(d, tag_page(old)) : dv_fill;
+  const bool split = wb && fill && dv_wb != dv_fill;
   uint32_t q = 0, slot = 0, ticket = 0;
-  uint32_t nslots = (wb ? 1u : 0u) + (fill ? 1u : 0u);
-  if (nslots && !sq_reserve_any(d, q0, nslots, q, slot, ticket)) {
+  uint32_t nslots = split ? 1u : (wb ? 1u : 0u) + (fill ? 1u : 0u);
+  if (nslots && !sq_reserve_dev(d, q0, wb ? dv_wb : dv_fill, nslots, q, slot, ticket)) {
     cache_unclaim(d, line, old);
     if (wb) sh_remove(d, (uint64_t)sh_wb);
     if (fill) sh_remove(d, (uint64_t)sh);
     return M_RETRY;
   }
+  uint32_t fq = q, fslot = slot, fticket = ticket;  // the read's slot
+  if (split && !sq_reserve_dev(d, q0, dv_fill, 1, fq, fslot, fticket)) {
+    sq_commit(d, q, slot, ticket, OP_FLUSH, 0, 0, ctx_make(CTX_NOP, 0, 0));
+    cache_unclaim(d, line, old);
+    sh_remove(d, (uint64_t)sh_wb);
+    sh_remove(d, (uint64_t)sh);
+    is.q = q;  // the no-op is rung like any command
+    is.slot = slot;
+    is.ticket = ticket;
+    is.q2 = 0xFFFFFFFFu;
+    return M_RETRY_RING;
+  }
   is.q = q;
   is.slot = slot;
   is.ticket = ticket;
+  is.q2 = 0xFFFFFFFFu;
   is.code = wb ? 3 : (old ? 2 : 1);
   if (old) atomicAdd(stat_ptr(d, S_EVICTIONS), 1ull);
   if (wb) {
@@ -578,8 +666,17 @@ static __device__ int cache_miss(const Dev &d, uint64_t page, uint32_t q0, uint3
               ctx_make(CTX_WB, (uint32_t)sh_wb, 0));
     atomicAdd(stat_ptr(d, S_WRITEBACKS), 1ull);
     if (!fill) return M_ISSUED;  // the write-back is the command to ring
-    slot = (slot + 1) & d.dmask;
-    ticket += 1;
+    if (split) {
+      is.q2 = q;  // ring the write-back's queue too; the read is the request's command
+      is.slot2 = slot;
+      is.ticket2 = ticket;
+      q = fq;
+      slot = fslot;
+      ticket = fticket;
+    } else {
+      slot = (slot + 1) & d.dmask;
+      ticket += 1;
+    }
   }
   if (!fill) {
     is.q = 0xFFFFFFFFu;  // nothing to ring
@@ -587,10 +684,22 @@ static __device__ int cache_miss(const Dev &d, uint64_t page, uint32_t q0, uint3
   }
   sq_commit(d, q, slot, ticket, OP_READ, (uint64_t)line_ptr(d, line), page,
             ctx_make(CTX_FILL, (uint32_t)sh, line));
+  // the read's token, for threads that find the page in flight (Sec. 3.4 case (c))
+  st_rel64(&d.sh_val[sh], ((uint64_t)q << 48) | ((uint64_t)slot << 32) | ticket);
   atomicAdd(stat_ptr(d, S_MISSES), 1ull);
+  is.q = q;
   is.slot = slot;
   is.ticket = ticket;
   return M_ISSUED;
+}
+
+// warp_ring for what cache_miss committed: the command (q, slot, ticket) and, when a
+// write-back went to another device's queue, that one too.
+__device__ __forceinline__ bool warp_ring_is(const Dev &d, bool has, const Issued &is, uint64_t deadline) {
+  bool ok = warp_ring(d, has, is.q, is.slot, is.ticket, deadline);
+  bool two = has && is.q2 != 0xFFFFFFFFu;
+  if (__any_sync(kFull, two)) ok = warp_ring(d, two, is.q2, is.slot2, is.ticket2, deadline) && ok;
+  return ok;
 }
 
 __device__ __forceinline__ uint64_t make_token(uint32_t q, uint32_t slot, uint32_t ticket) {
@@ -607,8 +716,11 @@ __device__ __forceinline__ uint64_t make_token(uint32_t q, uint32_t slot, uint32
 // wait=true it returns once every page is READY (no pins are held while waiting).
 // Returns false on timeout/abort.  `tok` (leaders) receives the token of the read the
 // lane itself issued, AGILE_TOKEN_HIT otherwise.
+// `all_hit` (optional) receives, in every lane, whether every leader's page was
+// READY at its first probe (the request had nothing to do).
 static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint32_t q0, bool wait,
-                             uint64_t deadline, uint64_t *tok = nullptr, int *code = nullptr) {
+                             uint64_t deadline, uint64_t *tok = nullptr, int *code = nullptr,
+                             bool *all_hit = nullptr) {
   unsigned grp = __match_any_sync(kFull, want ? page : ~0ull);
   int lead_lane = __ffs(grp) - 1;
   bool leader = want && lead_lane == (int)lane_id();
@@ -621,11 +733,14 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
   uint32_t retries = 0;
   if (tok && leader) *tok = ~0ull;
   if (code && leader) *code = 0;
+  bool first_miss = false;
   while (__any_sync(kFull, need)) {
-    bool issued = false;
+    bool issued = false, ring = false;
     Issued is{};
+    is.q2 = 0xFFFFFFFFu;
     if (need) {
       int pr = cache_probe(d, page, false, line);
+      if (first && pr != P_HIT) first_miss = true;
       if (pr == P_HIT) {
         need = false;
         if (first) atomicAdd(stat_ptr(d, S_HITS), 1ull);
@@ -634,6 +749,7 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
         if (!wait) need = false;
       } else {
         int m = cache_miss(d, page, q0, line, is);
+        ring = m == M_ISSUED || m == M_RETRY_RING;
         if (m == M_ISSUED) {
           issued = true;
           if (tok) *tok = make_token(is.q, is.slot, is.ticket);
@@ -649,7 +765,7 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
       }
     }
     first = false;
-    if (!warp_ring(d, issued, is.q, is.slot, is.ticket, deadline)) ok = false;
+    if (!warp_ring_is(d, ring, is, deadline)) ok = false;
     if (__any_sync(kFull, need)) {
       if (need) {
         if (gtimer() > deadline || aborted(d)) {
@@ -666,6 +782,7 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
       }
     }
   }
+  if (all_hit) *all_hit = !__any_sync(kFull, first_miss);
   return __all_sync(kFull, ok);
 }
 
@@ -734,6 +851,32 @@ static __device__ bool warp_pin_page(const Dev &d, uint64_t page, uint32_t q0, u
   }
 }
 
+// Asynchronous requests ahead of use pay a probe per page even when every page is
+// already resident.  A warp whose requests keep finding nothing to do requests less
+// often: after a round in which every page was resident it skips the next `span`
+// rounds (span 1, 3, 7, ... up to 63), and any round that found work, or any miss met
+// later by the warp's own gather, brings it back to every round.  Skipped pages are
+// fetched when used, as in synchronous mode.
+struct Backoff {
+  uint32_t skip = 0, span = 0;
+  __device__ __forceinline__ bool take() {  // true: request this round
+    if (skip) {
+      --skip;
+      return false;
+    }
+    return true;
+  }
+  __device__ __forceinline__ void result(bool all_hit) {
+    if (all_hit) {
+      span = span < 63 ? 2 * span + 1 : 63;
+      skip = span;
+    } else {
+      span = 0;
+    }
+  }
+  __device__ __forceinline__ void missed() { skip = span = 0; }
+};
+
 // what an application warp knows about its launch
 struct AppCtx {
   uint32_t warp;     // app warp index in [0, n_warps)
@@ -741,6 +884,106 @@ struct AppCtx {
   uint32_t q0;       // this lane's home queue (Sec. 3.3.1: by thread index)
   uint64_t deadline;
 };
+
+// ================================================================ user kernel API
+// The device side of Listing 1 (Sec. 3.5) for kernels that run inside a library launch
+// (agile_device.cuh launches them): a warp's lanes issue reads, continue with other
+// work, test or wait for each read's token, then copy the page.  No call here waits
+// while it holds a cache line or a queue slot.
+
+// Token state (agile_test): 0 done, AGILE_EIO done with an error, 1 still in flight.
+__device__ __forceinline__ int token_state(const Dev &d, uint64_t tok) {
+  if (tok == ~0ull) return 0;
+  uint32_t q = (uint32_t)(tok >> 48), slot = (uint32_t)(tok >> 32) & 0xFFFFu, ticket = (uint32_t)tok;
+  if (q >= d.Q || slot >= d.depth) return -22;
+  uint64_t w = ld_acq64(&d.cmpl[(uint64_t)q * d.depth + slot]);
+  uint32_t wt = (uint32_t)(w >> 32);
+  if (!(w & 1) || (int32_t)(wt - ticket) < 0) return 1;
+  // a later command of the slot has completed: this one completed before it
+  if (wt == ticket && ((w >> 1) & 0x7FFF) != 0) return -5;
+  return 0;
+}
+
+// asyncRead, issue part (warp-collective): lanes with `want` request `page`.  The
+// pages of equal requests are merged (the lowest lane goes to the cache); nothing waits
+// for data.  Returns the lane's token: AGILE_TOKEN_HIT (~0) when the page was READY,
+// else the token of the read that fills it -- issued here, or found in flight (the
+// share table names it).  ~0 too after a deadline or an abort (the data is then fetched
+// by agile_copy_page).
+static __device__ uint64_t api_issue_read(const Dev &d, const AppCtx &a, bool want, uint64_t page) {
+  unsigned grp = __match_any_sync(kFull, want ? page : ~0ull);
+  int lead = __ffs(grp) - 1;
+  bool leader = want && lead == (int)lane_id();
+  uint64_t tok = ~0ull;
+  bool need = leader;
+  uint32_t ns = 64;
+  while (__any_sync(kFull, need)) {
+    bool ring = false;
+    Issued is{};
+    is.q2 = 0xFFFFFFFFu;
+    if (need) {
+      uint32_t line = 0;
+      int pr = cache_probe(d, page, false, line);
+      if (pr == P_HIT) {
+        need = false;
+      } else if (pr == P_BUSY) {
+        uint64_t t = sh_token(d, page);
+        if (t) {
+          tok = t;
+          need = false;
+        }
+      } else {
+        int m = cache_miss(d, page, a.q0, line, is);
+        ring = m == M_ISSUED || m == M_RETRY_RING;
+        if (m == M_ISSUED) {
+          tok = make_token(is.q, is.slot, is.ticket);
+          need = false;
+        } else if (m == M_HIT) {
+          need = false;
+        }
+      }
+      if (need && (gtimer() > a.deadline || aborted(d))) need = false;
+    }
+    warp_ring_is(d, ring, is, a.deadline);
+    if (__any_sync(kFull, need)) backoff(ns, 1024);
+  }
+  tok = __shfl_sync(kFull, tok, lead & 31);
+  return want ? tok : ~0ull;
+}
+
+// agile_test: non-blocking ("continue" while it is 1)
+__device__ __forceinline__ int api_test(const Dev &d, uint64_t tok) { return token_state(d, tok); }
+
+// agile_wait: the transaction barrier of Sec. 3.2.1 for one token, bounded: 0 done,
+// AGILE_EIO done with an error, AGILE_ETIMEDOUT when `deadline_ns` (%globaltimer) passes
+// first.  The caller holds no pin while it waits (the library never does); a timeout
+// is returned to the caller and recorded nowhere else.
+__device__ __forceinline__ int api_wait(const Dev &d, uint64_t tok, uint64_t deadline_ns) {
+  uint32_t ns = 64;
+  for (;;) {
+    int st = token_state(d, tok);
+    if (st != 1) return st;
+    if (gtimer() > deadline_ns) return -110;
+    backoff(ns, 1024);
+  }
+}
+
+// Copy a page (uniform across the warp) from its cache line into dst (4096 bytes,
+// 16-byte aligned), with the line pinned for the copy only; a page evicted since its
+// read completed is requested again.  False on a timeout of the launch.
+static __device__ bool api_copy_page(const Dev &d, const AppCtx &a, uint64_t page, void *dst) {
+  uint32_t line;
+  if (!warp_pin_page<true>(d, page, a.q0, a.deadline, line)) return false;
+  warp_copy_page(dst, line_ptr(d, line));
+  __syncwarp();
+  if (lane_id() == 0) cache_unpin(d, line);
+  return true;
+}
+
+// prefetch (Listing 1 Method-1): start filling the pages of the lanes with `want`.
+static __device__ bool api_prefetch(const Dev &d, const AppCtx &a, bool want, uint64_t page) {
+  return warp_request_call(d, want, page, a.q0, false, a.deadline);
+}
 
 // Add rows [j0, j0 + k) (lane j holds row j's line `line_j` and byte offset `off`) to acc
 // in increasing j, with several rows' loads in flight at once.
@@ -787,9 +1030,10 @@ __device__ __forceinline__ void sum_rows(const Dev &d, uint32_t j0, uint32_t k, 
 // warp requests all missing pages without waiting, then waits for and pins that one
 // page (nothing else pinned meanwhile, Sec. 2.3.2) and adds its row: every round adds
 // at least one row, whatever the set conflicts among the rows.
+// `missed` (optional) is set in every lane when some page had to be requested.
 template <int MF4>
 static __device__ bool gather_sum(const Dev &d, const AppCtx &a, uint32_t begin, uint32_t cnt, uint64_t pg, uint32_t off,
-                           uint32_t nf4, float4 (&acc)[MF4]) {
+                           uint32_t nf4, float4 (&acc)[MF4], bool *missed = nullptr) {
   unsigned l = lane_id();
   uint32_t j0 = begin;
   bool first = true;
@@ -818,6 +1062,7 @@ static __device__ bool gather_sum(const Dev &d, const AppCtx &a, uint32_t begin,
       continue;
     }
     // row j0's page is missing: request every missing page, then wait for row j0's
+    if (missed) *missed = true;
     if (!warp_request(d, leader && pr != P_HIT, pg, a.q0, false, a.deadline)) return false;
     uint64_t pj = __shfl_sync(kFull, pg, j0 & 31);
     uint32_t lj;
@@ -930,13 +1175,16 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 // posts the CQEs {SQ head, SQ id, CID, status, phase}.  Commands of one queue complete
 // in any order, as NVMe allows.
 constexpr uint32_t kEmuBatch = 2;
+constexpr uint64_t kEmuSlackNs = 16000;
 
 static __device__ uint32_t emu_serve(const Dev &d, uint32_t q) {
   unsigned l = lane_id();
   uint32_t *es = &d.emu[q * 4];
   uint32_t f = 0, k = 0;
   uint64_t now = gtimer();
-  if (l == 0 && d.lat_ns == 0 && d.ns_per_page == 0) {
+  const uint32_t dv = d.ndev > 1 ? q % d.ndev : 0u;  // the device this queue belongs to
+  const bool model = d.lat_ns || d.ns_per_page || d.ns_rd_dev || d.ns_wr_dev;
+  if (l == 0 && !model) {
     // no latency model: every command the doorbell exposes is due at once.  The fetch
     // counter is read before the doorbell, so with f still current (checked by the
     // compare-and-swap) the doorbell is at most depth-1 commands ahead of it and
@@ -969,16 +1217,45 @@ static __device__ uint32_t emu_serve(const Dev &d, uint32_t q) {
         if (now < arr + d.lat_ns) break;
         ++k;
       }
-      if (k && d.ns_per_page) {
+      // Throughput: the batch is booked on the queue's pipe and on its device when each
+      // is free (reads and writes take device time of their own).  Bookings follow each
+      // other without gaps while the pipe has been idle for less than kEmuSlackNs
+      // (engines poll in turns, so a pipe's next batch is picked up a little late): a
+      // token bucket that may run kEmuSlackNs ahead after a pause, which moves the
+      // long-run rate by less than kEmuSlackNs per pause.  Bookings of a batch that is
+      // not served after all (another booking failed, or another engine took the
+      // commands meanwhile) are given back.
+      uint64_t qcost = d.ns_per_page * k, dcost = 0;
+      bool qbooked = false, dbooked = false;
+      if (k && qcost) {
         uint64_t busy = ld_rlx64(&d.emu_busy[q]);
         if (busy > now) {
           k = 0;
         } else {
-          uint64_t nb = now + d.ns_per_page * k;
-          if (atomicCAS(&d.emu_busy[q], (unsigned long long)busy, (unsigned long long)nb) != busy) k = 0;
+          uint64_t nb = (busy + kEmuSlackNs > now ? busy : now) + qcost;
+          qbooked = atomicCAS(&d.emu_busy[q], (unsigned long long)busy, (unsigned long long)nb) == busy;
+          if (!qbooked) k = 0;
+        }
+      }
+      if (k && (d.ns_rd_dev || d.ns_wr_dev)) {
+        for (uint32_t i = 0; i < k; ++i) {
+          uint32_t op = ld_rlx32(&d.sq[(uint64_t)q * d.depth + ((f + i) & d.dmask)].dw[0]) & 0xFFu;
+          dcost += op == OP_WRITE ? d.ns_wr_dev : (op == OP_READ ? d.ns_rd_dev : 0);
+        }
+        uint64_t busy = ld_rlx64(&d.dev_busy[dv]);
+        if (busy > now) {
+          k = 0;
+        } else {
+          uint64_t nb = (busy + kEmuSlackNs > now ? busy : now) + dcost;
+          dbooked = atomicCAS(&d.dev_busy[dv], (unsigned long long)busy, (unsigned long long)nb) == busy;
+          if (!dbooked) k = 0;
         }
       }
       if (k && atomicCAS(&es[0], f, f + k) != f) k = 0;
+      if (!k) {
+        if (qbooked) atomicAdd(&d.emu_busy[q], (unsigned long long)(-(int64_t)qcost));
+        if (dbooked && dcost) atomicAdd(&d.dev_busy[dv], (unsigned long long)(-(int64_t)dcost));
+      }
     }
   }
   k = __shfl_sync(kFull, k, 0);
@@ -999,7 +1276,9 @@ static __device__ uint32_t emu_serve(const Dev &d, uint32_t q) {
     nlb = (uint32_t)g.x & 0xFFFFu;
     uint32_t opcode = dw0 & 0xFFu;
     uint64_t nbytes = ((uint64_t)nlb + 1) * 512;
-    if (opcode != OP_FLUSH && (slba * 512 + nbytes > d.store_bytes || nbytes != kPage)) status = 0x80;
+    // from here on slba is the store page of the command (block on device dv)
+    slba = (d.ndev > 1 ? (slba / (kPage / 512)) * d.ndev + dv : slba / (kPage / 512));
+    if (opcode != OP_FLUSH && (slba * kPage + nbytes > d.store_bytes || nbytes != kPage)) status = 0x80;
     if (d.fault_flags) {
       uint64_t h = mix64(d.seed ^ ((uint64_t)q << 40) ^ (uint64_t)(f + l));
       if ((uint32_t)(h >> 32) < d.fault_thresh) {
@@ -1018,8 +1297,8 @@ static __device__ uint32_t emu_serve(const Dev &d, uint32_t q) {
     uint32_t stj = __shfl_sync(kFull, status, j);
     uint64_t pj = __shfl_sync(kFull, prp1, j), sj = __shfl_sync(kFull, slba, j);
     mv[j] = j < k && stj == 0 && (opj == OP_READ || opj == OP_WRITE);
-    srcs[j] = opj == OP_READ ? (uint64_t)(d.store + sj * 512) : pj;
-    dsts[j] = opj == OP_READ ? pj : (uint64_t)(d.store + sj * 512);
+    srcs[j] = opj == OP_READ ? (uint64_t)(d.store + sj * kPage) : pj;
+    dsts[j] = opj == OP_READ ? pj : (uint64_t)(d.store + sj * kPage);
     if (mv[j]) {
       const int4 *sp = (const int4 *)srcs[j];
 #pragma unroll
@@ -1037,6 +1316,12 @@ static __device__ uint32_t emu_serve(const Dev &d, uint32_t q) {
       else ++wr;
     }
   }
+  // per-page accounting of the data moved (lane i counts command i)
+  if (l < k && status == 0) {
+    uint32_t opcode = dw0 & 0xFFu;
+    if (opcode == OP_READ) atomicAdd(&d.pg_reads[slba], 1u);
+    else if (opcode == OP_WRITE) atomicAdd(&d.pg_writes[slba], 1u);
+  }
   __threadfence();
   __syncwarp();
   // completion entries
@@ -1049,6 +1334,22 @@ static __device__ uint32_t emu_serve(const Dev &d, uint32_t q) {
     uint32_t phase = ((sl / d.cq_size) & 1u) ^ 1u;
     Cqe *c = &d.cq[(uint64_t)q * d.cq_size + pos];
     uint32_t cid = dw0 >> 16;
+    if (d.trace) {
+      uint32_t ti = atomicAdd(d.trace_n, 1u);
+      if (ti < d.trace_cap) {
+        TraceRec *tr = &d.trace[ti];
+        tr->page = slba;
+        tr->t_seen = model
+                         ? ld_rlx64(&d.emu_arrival[(uint64_t)q * d.depth + ((f + l) & d.dmask)])
+                         : 0ull;
+        tr->t_start = now;
+        tr->t_done = gtimer();
+        tr->q = q;
+        tr->cid = cid;
+        tr->opcode = dw0 & 0xFFu;
+        tr->status = status | (drop ? 0x10000u : 0u);
+      }
+    }
     if (drop) {
       // the completion is lost; leave a harmless entry with the old phase
       st_rlx32(&c->dw[2], (q << 16) | ((f + l + 1) & d.dmask));

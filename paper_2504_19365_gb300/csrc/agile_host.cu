@@ -2,6 +2,7 @@
 // asyncRead / asyncWrite / wait / prefetch / flush / invalidate / replay.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -117,7 +118,9 @@ struct WriteApp {
       int how = -1;  // 0 pinned hit, 1 claimed
       Issued is{};
       is.q = 0xFFFFFFFFu;
+      is.q2 = 0xFFFFFFFFu;
       for (;;) {
+        bool noop = false;
         if (l == 0) {
           int pr = cache_probe(d, page, true, line);
           if (pr == P_HIT) {
@@ -125,12 +128,14 @@ struct WriteApp {
           } else if (pr == P_MISS) {
             int m = cache_miss(d, page, a.q0, line, is, false, sh);
             how = (m == M_ISSUED) ? 1 : -1;
+            noop = m == M_RETRY_RING;
           } else {
             how = -1;
           }
         }
         how = __shfl_sync(kFull, how, 0);
         if (how >= 0) break;
+        if (!warp_ring_is(d, noop, is, a.deadline)) return;
         if (gtimer() > a.deadline || aborted(d)) {
           if (l == 0) {
             set_error(d, -110);
@@ -141,26 +146,37 @@ struct WriteApp {
         backoff(ns);
       }
       line = __shfl_sync(kFull, line, 0);
-      uint32_t wq = __shfl_sync(kFull, is.q, 0), wslot = __shfl_sync(kFull, is.slot, 0),
-               wticket = __shfl_sync(kFull, is.ticket, 0);
-      if (!warp_ring(d, l == 0 && wq != 0xFFFFFFFFu, wq, wslot, wticket, a.deadline)) return;
+      if (!warp_ring_is(d, l == 0 && is.q != 0xFFFFFFFFu, is, a.deadline)) return;
       // 3. new contents into the line; publish it READY (a full page supersedes it)
       warp_copy_page(line_ptr(d, line), src + i * kPage);
       __threadfence();
       __syncwarp();
+      // The line stays pinned until the write is decided, so that it still holds this
+      // page when it is marked MODIFIED below.  A MODIFIED line's pending write is
+      // superseded by this page's write; otherwise the page now owes the store a write.
       if (l == 0) {
+        bool was_dirty = false;
         if (how == 0) {
-          atomicAnd(&d.tag[line], ~1ull);  // MODIFIED (3) or READY (2) -> READY
-          cache_unpin(d, line);
+          uint64_t old = atomicAnd(&d.tag[line], ~1ull);  // MODIFIED (3) or READY (2) -> READY
+          was_dirty = tag_state(old) == ST_MODIFIED;
         } else {
-          atomicAdd(&d.tag[line], 1ull);  // BUSY -> READY
+          atomicAdd(&d.tag[line], 1ull + PIN1);  // BUSY -> READY, pinned
         }
+        if (!was_dirty) note_dirty(d, page);
       }
-      // 4. write command from a staging copy
+      // 4. write command from a staging copy.  A reservation can fail under contention
+      // as well as on full queues, so it is retried for a while (slots are freed by
+      // completions, which never need a cache line) before the write is left to a
+      // later write-back of the MODIFIED line.
       uint32_t q = 0, slot = 0, ticket = 0;
       int ok = 0;
-      if (l == 0) ok = sq_reserve_any(d, a.q0, 1, q, slot, ticket);
-      ok = __shfl_sync(kFull, ok, 0);
+      uint32_t ns2 = 64;
+      for (int tries = 0; tries < 48; ++tries) {
+        if (l == 0) ok = sq_reserve_dev(d, a.q0, dev_of_page(d, page), 1, q, slot, ticket);
+        ok = __shfl_sync(kFull, ok, 0);
+        if (ok || aborted(d)) break;
+        backoff(ns2, 2048);
+      }
       uint64_t t = AGILE_TOKEN_HIT;
       if (ok) {
         q = __shfl_sync(kFull, q, 0);
@@ -173,12 +189,14 @@ struct WriteApp {
         if (l == 0) {
           sq_commit(d, q, slot, ticket, OP_WRITE, (uint64_t)stg, page, ctx_make(CTX_WB, (uint32_t)sh, 0));
           atomicAdd(stat_ptr(d, S_WRITEBACKS), 1ull);
+          cache_unpin(d, line);
         }
         if (!warp_ring(d, l == 0, q, slot, ticket, a.deadline)) return;
         t = make_token(q, slot, ticket);
       } else if (l == 0) {
         // no queue slot: keep the data as a MODIFIED line, written back later
         atomicOr(&d.tag[line], 1ull);
+        cache_unpin(d, line);
         sh_remove(d, (uint64_t)sh);
       }
       if (tok && l == 0) tok[i] = t;
@@ -212,7 +230,7 @@ struct FlushApp {
                 // readers and cannot be evicted until the write completes
                 uint64_t clean = (t & ~1ull) | TAG_WB;
                 if (atomicCAS(&d.tag[line], (unsigned long long)t, (unsigned long long)clean) == t) {
-                  if (sq_reserve_any(d, a.q0, 1, q, slot, ticket)) {
+                  if (sq_reserve_dev(d, a.q0, dev_of_page(d, tag_page(t)), 1, q, slot, ticket)) {
                     mine = true;
                   } else {
                     atomicOr(&d.tag[line], 1ull);
@@ -271,9 +289,10 @@ struct ReplayApp {
       }
       uint32_t ns = 64;
       for (;;) {
-        int done = 0, issued = 0;
+        int done = 0, issued = 0, ring = 0;
         uint32_t line = 0;
         Issued is{};
+        is.q2 = 0xFFFFFFFFu;
         if (l == 0) {
           int pr = cache_probe(d, page, false, line);
           if (pr == P_HIT) {
@@ -281,6 +300,7 @@ struct ReplayApp {
             atomicAdd(stat_ptr(d, S_HITS), 1ull);
           } else if (pr == P_MISS) {
             int m = cache_miss(d, page, a.q0, line, is);
+            ring = m == M_ISSUED || m == M_RETRY_RING;
             if (m == M_ISSUED) {
               issued = 1;
               code = is.code;
@@ -290,7 +310,7 @@ struct ReplayApp {
         done = __shfl_sync(kFull, done, 0);
         if (done) break;
         issued = __shfl_sync(kFull, issued, 0);
-        if (!warp_ring(d, l == 0 && issued, is.q, is.slot, is.ticket, a.deadline)) return;
+        if (!warp_ring_is(d, l == 0 && ring, is, a.deadline)) return;
         if (issued) {
           // wait for the fill with nothing held
           line = __shfl_sync(kFull, line, 0);
@@ -340,6 +360,24 @@ __global__ void wait_kernel(Dev d, const uint64_t *tok, uint32_t n, int32_t *sta
   } else {
     status[i] = 0;
   }
+}
+
+// Streams n16 16-byte words from pinned host memory (mapped) into HBM: each thread keeps
+// four loads in flight, the grid strides over the buffer.
+__global__ void link_probe_kernel(const uint8_t *src, uint8_t *dst, uint64_t n16) {
+  const int4 *s = (const int4 *)src;
+  int4 *t = (int4 *)dst;
+  uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n16; i += 4 * stride) {
+    int4 v0 = ld_cg16(s + i), v1 = ld_cg16(s + i + stride), v2 = ld_cg16(s + i + 2 * stride),
+         v3 = ld_cg16(s + i + 3 * stride);
+    st_cg16(t + i, v0);
+    st_cg16(t + i + stride, v1);
+    st_cg16(t + i + 2 * stride, v2);
+    st_cg16(t + i + 3 * stride, v3);
+  }
+  for (; i < n16; i += stride) st_cg16(t + i, ld_cg16(s + i));
 }
 
 __global__ void invalidate_range_kernel(Dev d, uint64_t p0, uint64_t p1) {
@@ -406,6 +444,10 @@ int agile_init(const agile_config *cfg_in, agile_ctx **out) {
   uint64_t sets = cfg.cache_bytes / ((uint64_t)cfg.ways * kPage);
   if (sets == 0 || sets > 0xFFFFFFFFull) return AGILE_EINVAL;
   if (cfg.fault_rate < 0 || cfg.fault_rate > 1 || cfg.emu_queue_gbps < 0) return AGILE_EINVAL;
+  if (cfg.emu_device_read_gbps < 0 || cfg.emu_device_write_gbps < 0) return AGILE_EINVAL;
+  if (cfg.num_devices == 0) cfg.num_devices = 1;
+  if (cfg.num_devices > cfg.num_queues || cfg.num_queues % cfg.num_devices) return AGILE_EINVAL;
+  if (cfg.cache_policy > AGILE_POLICY_FIFO) return AGILE_EINVAL;
   if (cfg.wait_timeout_ns == 0) cfg.wait_timeout_ns = 10ull * 1000 * 1000 * 1000;
   if (cfg.prefetch_depth == 0) cfg.prefetch_depth = 1;
 
@@ -477,6 +519,16 @@ int agile_init(const agile_config *cfg_in, agile_ctx **out) {
   d.emu_busy = (unsigned long long *)A(Q * 8);
   d.emu_arrival = (unsigned long long *)A(Q * D * 8);
   d.staging = (uint8_t *)A(Q * D * kPage);
+  uint64_t store_pages = cfg.store_bytes / kPage;
+  d.pg_reads = (uint32_t *)A(store_pages * 4);
+  d.pg_writes = (uint32_t *)A(store_pages * 4);
+  d.pg_dirty = (uint32_t *)A(store_pages * 4);
+  d.trace_cap = cfg.trace_records;
+  d.trace = cfg.trace_records ? (TraceRec *)A((uint64_t)cfg.trace_records * sizeof(TraceRec)) : nullptr;
+  d.trace_n = (uint32_t *)A(16);
+  d.ndev = cfg.num_devices;
+  d.policy = cfg.cache_policy;
+  d.dev_busy = (unsigned long long *)A((uint64_t)cfg.num_devices * 8);
   d.run = (RunState *)A(sizeof(RunState));
   d.stats = (unsigned long long *)A((size_t)kStatShards * S_COUNT * 8);
   d.err_sticky = (int32_t *)A(16);
@@ -495,6 +547,8 @@ int agile_init(const agile_config *cfg_in, agile_ctx **out) {
   }
   d.lat_ns = cfg.emu_latency_ns;
   d.ns_per_page = cfg.emu_queue_gbps > 0 ? (uint64_t)llround(kPage / cfg.emu_queue_gbps) : 0;
+  d.ns_rd_dev = cfg.emu_device_read_gbps > 0 ? (uint64_t)llround(kPage / cfg.emu_device_read_gbps) : 0;
+  d.ns_wr_dev = cfg.emu_device_write_gbps > 0 ? (uint64_t)llround(kPage / cfg.emu_device_write_gbps) : 0;
   d.fault_flags = cfg.fault_flags;
   d.fault_thresh = (uint32_t)fmin(4294967295.0, cfg.fault_rate * 4294967296.0);
   d.seed = cfg.seed;
@@ -637,6 +691,116 @@ int agile_reset_stats(agile_ctx *c) {
   AGILE_CUDA_TRY(cudaSetDevice(c->device));
   AGILE_CUDA_TRY(cudaDeviceSynchronize());
   AGILE_CUDA_TRY(cudaMemset(c->dev.stats, 0, (size_t)kStatShards * S_COUNT * 8));
+  uint64_t pages = c->cfg.store_bytes / kPage;
+  AGILE_CUDA_TRY(cudaMemset(c->dev.pg_reads, 0, pages * 4));
+  AGILE_CUDA_TRY(cudaMemset(c->dev.pg_writes, 0, pages * 4));
+  AGILE_CUDA_TRY(cudaMemset(c->dev.pg_dirty, 0, pages * 4));
+  AGILE_CUDA_TRY(cudaMemset(c->dev.trace_n, 0, 4));
+  return AGILE_OK;
+}
+
+int agile_set_device_model(agile_ctx *c, uint32_t ndev, uint32_t lat_ns, double queue_gbps, double rd_gbps,
+                           double wr_gbps) {
+  if (!c) return AGILE_EINVAL;
+  if (ndev == 0) ndev = 1;
+  if (ndev > c->cfg.num_queues || c->cfg.num_queues % ndev) return AGILE_EINVAL;
+  if (queue_gbps < 0 || rd_gbps < 0 || wr_gbps < 0) return AGILE_EINVAL;
+  AGILE_CUDA_TRY(cudaSetDevice(c->device));
+  AGILE_CUDA_TRY(cudaDeviceSynchronize());
+  if (ndev > c->cfg.num_devices) {
+    // the per-device booking words: one per device
+    unsigned long long *nb = nullptr;
+    AGILE_CUDA_TRY(cudaMalloc(&nb, (size_t)ndev * 8));
+    c->dallocs.push_back(nb);
+    c->dev.dev_busy = nb;
+  }
+  AGILE_CUDA_TRY(cudaMemset(c->dev.dev_busy, 0, (size_t)ndev * 8));
+  AGILE_CUDA_TRY(cudaMemset(c->dev.emu_busy, 0, (size_t)c->dev.Q * 8));
+  c->cfg.num_devices = std::max(c->cfg.num_devices, ndev);
+  c->dev.ndev = ndev;
+  c->dev.lat_ns = lat_ns;
+  c->dev.ns_per_page = queue_gbps > 0 ? (uint64_t)llround(kPage / queue_gbps) : 0;
+  c->dev.ns_rd_dev = rd_gbps > 0 ? (uint64_t)llround(kPage / rd_gbps) : 0;
+  c->dev.ns_wr_dev = wr_gbps > 0 ? (uint64_t)llround(kPage / wr_gbps) : 0;
+  c->cfg.emu_latency_ns = lat_ns;
+  c->cfg.emu_queue_gbps = queue_gbps;
+  c->cfg.emu_device_read_gbps = rd_gbps;
+  c->cfg.emu_device_write_gbps = wr_gbps;
+  return AGILE_OK;
+}
+
+int agile_device_view(agile_ctx *c, void *out, uint64_t size) {
+  if (!c || !out || size != sizeof(Dev)) return AGILE_EINVAL;
+  AGILE_CUDA_TRY(cudaSetDevice(c->device));
+  Dev d = c->dev;
+  d.app_active = c->cfg.app_warps;
+  memcpy(out, &d, sizeof(Dev));
+  return AGILE_OK;
+}
+
+int agile_run_reset(agile_ctx *c, void *stream) {
+  if (!c) return AGILE_EINVAL;
+  AGILE_CUDA_TRY(cudaSetDevice(c->device));
+  run_reset_kernel<<<1, 128, 0, as_stream(stream)>>>(c->dev.run);
+  AGILE_CUDA_TRY(cudaGetLastError());
+  return AGILE_OK;
+}
+
+int agile_page_io(agile_ctx *c, uint64_t page0, uint64_t n, uint32_t *reads, uint32_t *writes, uint32_t *dirtied) {
+  if (!c) return AGILE_EINVAL;
+  uint64_t pages = c->cfg.store_bytes / kPage;
+  if (page0 > pages || n > pages - page0) return AGILE_EINVAL;
+  AGILE_CUDA_TRY(cudaSetDevice(c->device));
+  AGILE_CUDA_TRY(cudaDeviceSynchronize());
+  if (n == 0) return AGILE_OK;
+  if (reads) AGILE_CUDA_TRY(cudaMemcpy(reads, c->dev.pg_reads + page0, n * 4, cudaMemcpyDeviceToHost));
+  if (writes) AGILE_CUDA_TRY(cudaMemcpy(writes, c->dev.pg_writes + page0, n * 4, cudaMemcpyDeviceToHost));
+  if (dirtied) AGILE_CUDA_TRY(cudaMemcpy(dirtied, c->dev.pg_dirty + page0, n * 4, cudaMemcpyDeviceToHost));
+  return AGILE_OK;
+}
+
+int agile_trace(agile_ctx *c, agile_trace_rec *out, uint32_t cap, uint32_t *n_out) {
+  static_assert(sizeof(agile_trace_rec) == sizeof(TraceRec), "trace record layout");
+  if (!c || (cap && !out)) return AGILE_EINVAL;
+  AGILE_CUDA_TRY(cudaSetDevice(c->device));
+  AGILE_CUDA_TRY(cudaDeviceSynchronize());
+  uint32_t n = 0;
+  AGILE_CUDA_TRY(cudaMemcpy(&n, c->dev.trace_n, 4, cudaMemcpyDeviceToHost));
+  if (n_out) *n_out = n;
+  uint32_t k = std::min(std::min(n, c->dev.trace_cap), cap);
+  if (k) AGILE_CUDA_TRY(cudaMemcpy(out, c->dev.trace, (size_t)k * sizeof(TraceRec), cudaMemcpyDeviceToHost));
+  return AGILE_OK;
+}
+
+int agile_link_probe(agile_ctx *c, void *d_dst, uint64_t bytes, uint32_t ctas, uint32_t reps, double *gbps) {
+  if (!c || !d_dst || !gbps || bytes == 0 || bytes % kPage || bytes > c->cfg.store_bytes) return AGILE_EINVAL;
+  if (((uintptr_t)d_dst) & 15) return AGILE_EINVAL;
+  AGILE_CUDA_TRY(cudaSetDevice(c->device));
+  if (ctas == 0) ctas = 2u * (uint32_t)c->sms;
+  if (reps == 0) reps = 1;
+  cudaEvent_t a, b;
+  AGILE_CUDA_TRY(cudaEventCreate(&a));
+  AGILE_CUDA_TRY(cudaEventCreate(&b));
+  double best = 0;
+  for (uint32_t r = 0; r < reps; ++r) {
+    cudaEventRecord(a, 0);
+    link_probe_kernel<<<ctas, 512>>>(c->dev.store, (uint8_t *)d_dst, bytes / 16);
+    cudaEventRecord(b, 0);
+    cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      fprintf(stderr, "agile_link_probe: %s\n", cudaGetErrorString(e));
+      return AGILE_ECUDA;
+    }
+    if (ms > 0) best = std::max(best, bytes / (ms * 1e-3) / 1e9);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *gbps = best;
   return AGILE_OK;
 }
 

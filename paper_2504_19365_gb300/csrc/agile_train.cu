@@ -157,7 +157,8 @@ struct BackwardApp {
           __threadfence();
           __syncwarp();
           if (l == 0) {
-            atomicOr(&d.tag[line], 1ull);  // READY (2) -> MODIFIED (3)
+            uint64_t old = atomicOr(&d.tag[line], 1ull);  // READY (2) -> MODIFIED (3)
+            if (tag_state(old) == ST_READY) note_dirty(d, page0 + byte / kPage);
             cache_unpin(d, line);
           }
         }

@@ -217,5 +217,14 @@ def graph_uniform(seed: int, n: int, m: int):
     return csr_from_edges(n, s, d)
 
 
+def uniform_csr(seed: int, scale: int, edge_factor: int):
+    """Uniform random graph (Erdos-Renyi style, as GAP's uniform generator: every edge's
+    two endpoints drawn uniformly from the 2^scale vertices), edge_factor * 2^scale
+    edges, then symmetrised, self-loops dropped, duplicates removed, lists sorted."""
+    n = 1 << scale
+    offsets, cols = graph_uniform(seed, n, edge_factor << scale)
+    return n, offsets, cols
+
+
 def pages_for(nbytes: int) -> int:
     return (int(nbytes) + PAGE - 1) // PAGE

@@ -111,3 +111,46 @@ def test_tiny_ring_and_tiny_cache(mode):
         c.check()
         assert np.array_equal(lv.cpu().numpy(), want) and int(ed.item()) == scanned
         assert_cache_invariants(c)
+
+
+@pytest.mark.parametrize("mode", [ag.AGILE_SYNC, ag.AGILE_ASYNC])
+def test_uniform_random_graph_scale20(mode):
+    # the "-U" graphs of Sec. 4.5: every edge's endpoints uniform, scale 20, edge factor
+    # 16, cache 1/8 of the columns; 2 seeded sources
+    n, off, cols = synth.uniform_csr(8, 20, 16)
+    col0, total = _layout(off, cols)
+    with Ctx(total, cache_bytes=_cache_for(cols), ways=8) as c:
+        c.put(0, off)
+        c.put(col0, cols)
+        for src in synth.bfs_sources(8, off, 2):
+            lv, edges = _bfs(c, col0, n, src, mode)
+            want, scanned = oracle.bfs(off, cols, int(src))
+            assert np.array_equal(lv, want)
+            assert edges == scanned
+
+
+@pytest.mark.parametrize("graph", ["rmat", "uniform", "path"])
+def test_hbm_kernel_equals_oracle(graph):
+    # the breakdown's kernel-time baseline: the same kernel over the CSR in HBM
+    if graph == "rmat":
+        n, off, cols = synth.rmat_csr(3, 16, 16)
+    elif graph == "uniform":
+        n, off, cols = synth.uniform_csr(9, 16, 16)
+    else:
+        off, cols = synth.graph_path(5000)
+        n = off.size - 1
+    col0, total = _layout(off, cols)
+    with Ctx(total, cache_bytes=_cache_for(cols), ways=8) as c:
+        d_off = torch.from_numpy(off).to(DEV)
+        d_cols = torch.from_numpy(cols).to(DEV)
+        for src in synth.bfs_sources(10, off, 2):
+            level = torch.full((n,), 77, dtype=torch.int32, device=DEV)
+            edges = torch.zeros(1, dtype=torch.int64, device=DEV)
+            ag.agile_bfs_hbm(c.h, d_off.data_ptr(), d_cols.data_ptr(), n, int(cols.size), int(src),
+                             level.data_ptr(), edges.data_ptr(), c.stream)
+            torch.cuda.synchronize()
+            c.check()
+            want, scanned = oracle.bfs(off, cols, int(src))
+            assert np.array_equal(level.cpu().numpy(), want)
+            assert int(edges.item()) == scanned
+        assert c.stats()["commands"] == 0   # no page went through the queues

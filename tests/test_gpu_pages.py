@@ -125,7 +125,42 @@ def test_write_then_read_then_flush_store_equals_oracle():
         assert np.array_equal(c.get(0, store.nbytes), truth)
         s = c.stats()
         assert s["bytes_written"] == 4096 * s["writebacks"]
+        # every page written once by the device: one write per page write (or per
+        # dirty epoch of a page whose write found no queue slot), none for other pages
+        _, writes, dirtied = ag.agile_page_io(c.h, 0, npages)
+        assert np.array_equal(writes, dirtied)
+        mask = np.zeros(npages, dtype=bool)
+        mask[wpages.astype(np.int64)] = True
+        assert (writes[mask] == 1).all() and (writes[~mask] == 0).all()
         assert_cache_invariants(c)
+
+
+@pytest.mark.parametrize("policy", [ag.AGILE_POLICY_CLOCK, ag.AGILE_POLICY_FIFO])
+@pytest.mark.parametrize("ndev", [1, 3])
+def test_replay_with_policy_and_devices_equals_reference_cache(policy, ndev):
+    # the same single-request replay for each replacement policy, with the pages spread
+    # over one or three backing devices (where a page lives changes no decision)
+    sets, ways, npages = 4, 4, 64
+    store = _store(npages, 13)
+    trace = np.concatenate([synth.uniform_int(17, 500, npages), np.tile(np.arange(ways + 1), 4),
+                            np.array([1, 2, 3, 4, 2, 5, 2] * 3)]).astype(np.uint64)
+    ref = oracle.RefCache(sets, ways, store.copy(), policy=policy)
+    want = ref.replay(trace)
+    with Ctx(store.nbytes, cache_bytes=sets * ways * 4096, ways=ways, num_queues=6, queue_depth=64,
+             cache_policy=policy, num_devices=ndev) as c:
+        c.put(0, store)
+        d_pages = torch.from_numpy(trace.view(np.int64)).to(DEV)
+        codes = torch.full((len(trace),), -1, dtype=torch.int32, device=DEV)
+        ag.agile_cache_replay(c.h, d_pages.data_ptr(), len(trace), codes.data_ptr(), c.stream)
+        torch.cuda.synchronize()
+        c.check()
+        got = codes.cpu().numpy()
+        assert np.array_equal(got, want), np.nonzero(got != want)[0][:10]
+        page, state, _, _ = tag_fields(c.tags())
+        opage, ostate, _ = ref.tags()
+        valid = ostate != 0
+        assert np.array_equal(state != 0, valid)
+        assert np.array_equal(page[valid], opage[valid])
 
 
 @pytest.mark.parametrize("mode", [ag.AGILE_SYNC, ag.AGILE_ASYNC])

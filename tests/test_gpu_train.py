@@ -81,9 +81,16 @@ def test_sgd_written_back_through_small_cache(mode):
         s = c.stats()
         assert s1["writebacks"] > 0, "evictions of MODIFIED lines during the call"
         assert s["bytes_written"] == 4096 * s["writebacks"]
-        # every dirtied page written back at least once, never more often than it was dirtied
-        pages_touched = len(np.unique((np.nonzero(touched)[0] * dim * 4) // 4096))
-        assert pages_touched <= s["writebacks"]
+        # the device's per-page write log: every dirty epoch of a page (a clean line of
+        # it turned MODIFIED) ended in exactly one write-back, and no other page was
+        # written; some pages went through several epochs (evicted, then dirtied again)
+        npages = T.nbytes // 4096
+        _, writes, dirtied = ag.agile_page_io(c.h, 0, npages)
+        hit = np.zeros(npages, dtype=bool)
+        hit[np.unique((np.nonzero(touched)[0] * dim * 4) // 4096)] = True
+        assert np.array_equal(writes, dirtied)
+        assert (dirtied[hit] >= 1).all() and (dirtied[~hit] == 0).all()
+        assert int(writes.sum()) == s["writebacks"]
         assert_cache_invariants(c)
         # a following forward sees the updated rows
         d_idx = torch.from_numpy(idx).to(DEV)

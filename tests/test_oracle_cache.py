@@ -185,3 +185,49 @@ def test_writeback_exactly_once_per_dirty_epoch():
     assert c.flush() == 1
     assert list(c.writeback_log()) == [5, 5]
     assert c.flush() == 0
+
+
+# ---------------------------------------------------------------- FIFO policy
+# First-in first-out replacement (the policy is the user's choice, Sec. 3.4).  Pins:
+# Belady's anomaly (Belady, Nelson and Shedler, CACM 1969), the textbook example in
+# which FIFO takes more misses with more frames, and brute force against a per-set
+# queue of pages written here.
+
+def test_fifo_belady_anomaly():
+    trace = np.array([1, 2, 3, 4, 1, 2, 5, 1, 2, 3, 4, 5], dtype=np.uint64)
+    misses = {}
+    for ways in (3, 4):
+        c = oracle.RefCache(1, ways, _store(8), policy=oracle.RefCache.FIFO)
+        codes = c.replay(trace)
+        misses[ways] = int((codes != oracle.HIT).sum())
+    assert misses == {3: 9, 4: 10}
+
+
+@pytest.mark.parametrize("sets,ways", [(1, 2), (1, 4), (4, 3), (8, 8)])
+def test_fifo_brute_force_queue(sets, ways):
+    import collections
+    npages = 40
+    pages = synth.uniform_int(31, 3000, npages)
+    c = oracle.RefCache(sets, ways, _store(npages), policy=oracle.RefCache.FIFO)
+    codes = c.replay(pages)
+    q = collections.defaultdict(collections.deque)   # per set: pages, oldest first
+    for i, p in enumerate(pages.tolist()):
+        dq = q[oracle.set_of(p, sets)]
+        if p in dq:
+            assert codes[i] == oracle.HIT, i
+        else:
+            assert codes[i] == (oracle.MISS_FILL if len(dq) < ways else oracle.MISS_EVICT), i
+            if len(dq) == ways:
+                dq.popleft()
+            dq.append(p)
+
+
+def test_fifo_differs_from_clock_on_reuse():
+    # 1, 2, 3 fill three ways; 4 replaces 1 (clock: after clearing every reference bit);
+    # 2 is used again; 5 must replace a page.  FIFO takes 2 (the oldest fill) although
+    # it was just used; clock gives 2 a second chance and takes 3
+    trace = np.array([1, 2, 3, 4, 2, 5, 2], dtype=np.uint64)
+    fifo = oracle.RefCache(1, 3, _store(8), policy=oracle.RefCache.FIFO).replay(trace)
+    clock = oracle.RefCache(1, 3, _store(8)).replay(trace)
+    assert fifo[-1] != oracle.HIT
+    assert clock[-1] == oracle.HIT

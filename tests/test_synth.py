@@ -46,3 +46,19 @@ def test_generators_deterministic():
     a = synth.rmat_csr(9, 9, 4)
     b = synth.rmat_csr(9, 9, 4)
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+def test_uniform_csr_is_a_simple_undirected_graph():
+    n, off, cols = synth.uniform_csr(3, 10, 8)
+    assert n == 1024 and off[0] == 0 and off[-1] == cols.size
+    src = np.repeat(np.arange(n), np.diff(off))
+    assert (src != cols).all()                                   # no self loops
+    pairs = set(zip(src.tolist(), cols.tolist()))
+    assert all((b, a) in pairs for a, b in pairs)               # symmetric
+    for v in range(n):
+        lst = cols[off[v]:off[v + 1]]
+        assert (np.diff(lst) > 0).all()                          # sorted, no duplicates
+    # about 2 * 8 * 1024 entries (a few duplicates and loops dropped); same seed, same graph
+    assert 0.95 * 2 * 8 * 1024 < cols.size <= 2 * 8 * 1024
+    n2, off2, cols2 = synth.uniform_csr(3, 10, 8)
+    assert np.array_equal(off, off2) and np.array_equal(cols, cols2)
