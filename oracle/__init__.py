@@ -65,6 +65,16 @@ def lib():
         L.orc_cache_wb_log.restype = u64
         L.orc_cache_tags.argtypes = [vp, vp, vp, vp]
         L.orc_cache_line.argtypes = [vp, u64, vp]
+        L.orc_share_new.argtypes = [vp, u32]
+        L.orc_share_new.restype = vp
+        L.orc_share_free.argtypes = [vp]
+        L.orc_share_acquire.argtypes = [vp, vp, vp, u64, i32]
+        L.orc_share_acquire.restype = i32
+        L.orc_share_write.argtypes = [vp, vp, u64, u32, vp, u32]
+        L.orc_share_release.argtypes = [vp, vp, vp, u64]
+        L.orc_share_release.restype = C.c_int
+        L.orc_share_entry.argtypes = [vp, u64, vp]
+        L.orc_share_counters.argtypes = [vp, vp]
         L.orc_embedding_bag.argtypes = [vp, u64, u32, vp, vp, u64, vp]
         L.orc_embedding_bag_backward.argtypes = [u64, u32, vp, vp, u64, vp, vp, vp]
         L.orc_sgd.argtypes = [vp, u64, u32, vp, vp, C.c_float]
@@ -173,6 +183,46 @@ class RefCache:
         out = np.empty(PAGE, dtype=np.uint8)
         lib().orc_cache_line(self.h, line, _p(out))
         return out
+
+
+# ----------------------------------------------------------------------------- share table
+
+UB_I, UB_E, UB_S, UB_M, UB_O = 0, 1, 2, 3, 4
+
+
+class ShareTable:
+    """Sequential Share Table (Sec. 3.4.1) over a RefCache; ``bufs`` is a uint8 array of
+    4096-byte user buffers named by index (modified in place)."""
+
+    def __init__(self, cache: RefCache, cap: int, bufs: np.ndarray):
+        assert bufs.dtype == np.uint8 and bufs.flags.c_contiguous
+        self.cache, self.bufs = cache, bufs
+        self.h = lib().orc_share_new(cache.h, cap)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_share_free(self.h)
+            self.h = None
+
+    def acquire(self, page: int, mine: int) -> int:
+        return int(lib().orc_share_acquire(self.h, _p(self.cache.store), _p(self.bufs), page, mine))
+
+    def write(self, page: int, off: int, data: np.ndarray) -> None:
+        d = _c(data, np.uint8)
+        lib().orc_share_write(self.h, _p(self.bufs), page, off, _p(d), d.size)
+
+    def release(self, page: int) -> bool:
+        return bool(lib().orc_share_release(self.h, _p(self.cache.store), _p(self.bufs), page))
+
+    def entry(self, page: int):
+        out = np.zeros(3, dtype=np.int32)
+        lib().orc_share_entry(self.h, page, _p(out))
+        return int(out[0]), int(out[1]), int(out[2])
+
+    def counters(self) -> dict:
+        out = np.zeros(3, dtype=np.uint64)
+        lib().orc_share_counters(self.h, _p(out))
+        return dict(store_reads=int(out[0]), cache_copies=int(out[1]), propagations=int(out[2]))
 
 
 # ----------------------------------------------------------------------------- embedding bag

@@ -15,6 +15,9 @@
  *                           states of Sec. 3.4 (INVALID / READY / MODIFIED; BUSY is never
  *                           observable when requests are served one at a time) and clock
  *                           replacement (Sec. 4.4 names the clock policy of Corbato 1968).
+ *   - share table         : user buffers shared by pointer with a reference count and
+ *                           MOESI-inspired states; a modified buffer is propagated into
+ *                           the cache by its last release (Sec. 3.4.1).
  *   - embedding bag       : sum pooling of table rows, one FP32 accumulator per output
  *                           element, indices added in increasing order (Sec. 4.4 DLRM
  *                           lookups); backward scatter-add and an SGD step.
@@ -266,6 +269,134 @@ void orc_cache_tags(const orc_cache *c, uint64_t *page, uint8_t *state, uint8_t 
 
 void orc_cache_line(const orc_cache *c, uint64_t line, uint8_t *out) {
   memcpy(out, c->data + line * ORC_PAGE, ORC_PAGE);
+}
+
+/* ------------------------------------------------------------------ share table */
+
+/*
+ * Share Table of Sec. 3.4.1 (user-specified buffers shared by pointer, MOESI-inspired),
+ * served one operation at a time.  An entry maps a page to the user buffer that holds
+ * it, with a reference count and a state:
+ *   E  one user, buffer equal to the page         S  several users, equal to the page
+ *   M  one user, buffer modified                  O  several users, buffer modified
+ *   (no entry = I)
+ * acquire(page, mine): if an entry holds the page, its buffer is returned and its count
+ *   goes up (E -> S, M -> O: the data is shared by pointer, nothing is copied); else
+ *   `mine` is registered (E, count 1) and filled with the page: from its cache line if
+ *   the cache holds it (a hit, which sets the line's reference bit), else straight from
+ *   the store (the cache is left as it is).
+ * write(page, off, data): into the entry's buffer; E -> M, S -> O.
+ * release(page): the count goes down; at zero a modified buffer (M or O) is propagated
+ *   into the software cache -- the page's line gets the buffer's bytes and turns
+ *   MODIFIED (case (d) writes it back later) -- and the entry goes away.  Who releases
+ *   last does this on the owner's behalf (the owner may have released first).
+ * Buffers are 4096-byte slots of `bufs`, named by index.
+ */
+enum { ORC_UB_I = 0, ORC_UB_E = 1, ORC_UB_S = 2, ORC_UB_M = 3, ORC_UB_O = 4 };
+
+typedef struct {
+  orc_cache *cache;
+  uint32_t cap;
+  uint64_t *page;
+  int32_t *buf;
+  uint32_t *ref;
+  uint8_t *state;
+  uint64_t store_reads, cache_copies, propagations;
+} orc_share;
+
+orc_share *orc_share_new(orc_cache *cache, uint32_t cap) {
+  orc_share *t = (orc_share *)calloc(1, sizeof(orc_share));
+  t->cache = cache;
+  t->cap = cap;
+  t->page = (uint64_t *)calloc(cap, sizeof(uint64_t));
+  t->buf = (int32_t *)calloc(cap, sizeof(int32_t));
+  t->ref = (uint32_t *)calloc(cap, sizeof(uint32_t));
+  t->state = (uint8_t *)calloc(cap, 1);
+  return t;
+}
+
+void orc_share_free(orc_share *t) {
+  if (!t) return;
+  free(t->page); free(t->buf); free(t->ref); free(t->state);
+  free(t);
+}
+
+static int64_t orc_share_find(const orc_share *t, uint64_t page) {
+  for (uint32_t i = 0; i < t->cap; ++i)
+    if (t->state[i] != ORC_UB_I && t->page[i] == page) return i;
+  return -1;
+}
+
+/* Returns the buffer now holding the page (-1 when the table is full). */
+int32_t orc_share_acquire(orc_share *t, uint8_t *store, uint8_t *bufs, uint64_t page, int32_t mine) {
+  int64_t e = orc_share_find(t, page);
+  if (e >= 0) {
+    t->ref[e] += 1;
+    if (t->state[e] == ORC_UB_E) t->state[e] = ORC_UB_S;
+    if (t->state[e] == ORC_UB_M) t->state[e] = ORC_UB_O;
+    return t->buf[e];
+  }
+  for (uint32_t i = 0; i < t->cap; ++i) {
+    if (t->state[i] != ORC_UB_I) continue;
+    t->page[i] = page;
+    t->buf[i] = mine;
+    t->ref[i] = 1;
+    t->state[i] = ORC_UB_E;
+    uint8_t *dst = bufs + (uint64_t)mine * ORC_PAGE;
+    orc_cache *c = t->cache;
+    uint32_t s = orc_set_of(page, c->sets);
+    uint64_t base = (uint64_t)s * c->ways;
+    for (uint32_t w = 0; w < c->ways; ++w) {
+      uint8_t st = c->state[base + w];
+      if ((st == ORC_READY || st == ORC_MODIFIED) && c->page[base + w] == page) {
+        memcpy(dst, c->data + (base + w) * ORC_PAGE, ORC_PAGE);
+        c->ref[base + w] = 1;
+        t->cache_copies++;
+        return mine;
+      }
+    }
+    memcpy(dst, store + page * ORC_PAGE, ORC_PAGE);
+    t->store_reads++;
+    return mine;
+  }
+  return -1;
+}
+
+/* Write into the buffer that holds `page` (which must be acquired). */
+void orc_share_write(orc_share *t, uint8_t *bufs, uint64_t page, uint32_t off, const uint8_t *data,
+                     uint32_t len) {
+  int64_t e = orc_share_find(t, page);
+  if (e < 0) return;
+  memcpy(bufs + (uint64_t)t->buf[e] * ORC_PAGE + off, data, len);
+  if (t->state[e] == ORC_UB_E) t->state[e] = ORC_UB_M;
+  if (t->state[e] == ORC_UB_S) t->state[e] = ORC_UB_O;
+}
+
+/* Returns 1 when this release propagated a modified buffer into the cache. */
+int orc_share_release(orc_share *t, uint8_t *store, uint8_t *bufs, uint64_t page) {
+  int64_t e = orc_share_find(t, page);
+  if (e < 0) return 0;
+  t->ref[e] -= 1;
+  if (t->ref[e] > 0) return 0;
+  int prop = t->state[e] == ORC_UB_M || t->state[e] == ORC_UB_O;
+  if (prop) {
+    orc_cache_write(t->cache, store, page, 0, ORC_PAGE, bufs + (uint64_t)t->buf[e] * ORC_PAGE, 0);
+    t->propagations++;
+  }
+  t->state[e] = ORC_UB_I;
+  return prop;
+}
+
+/* state (ORC_UB_*) and count of the entry holding `page` (I and 0 when none) */
+void orc_share_entry(const orc_share *t, uint64_t page, int32_t out[3]) {
+  int64_t e = orc_share_find(t, page);
+  out[0] = e >= 0 ? t->state[e] : ORC_UB_I;
+  out[1] = e >= 0 ? (int32_t)t->ref[e] : 0;
+  out[2] = e >= 0 ? t->buf[e] : -1;
+}
+
+void orc_share_counters(const orc_share *t, uint64_t out[3]) {
+  out[0] = t->store_reads; out[1] = t->cache_copies; out[2] = t->propagations;
 }
 
 /* ------------------------------------------------------------------ embedding bag */
