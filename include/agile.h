@@ -113,6 +113,8 @@ typedef struct {
   uint32_t cache_policy;    /* AGILE_POLICY_CLOCK (default) or AGILE_POLICY_FIFO      */
   double emu_device_read_gbps;   /* per-device read throughput cap, GB/s (0 = none)  */
   double emu_device_write_gbps;  /* per-device write throughput cap, GB/s (0 = none) */
+  uint32_t share_slots;     /* Share Table entries for user buffers (Sec. 3.4.1); 0 = no
+                               Share Table (it is an option, as in the paper)        */
 } agile_config;
 
 /* Replacement policies of the cache (Sec. 3.4 leaves the policy to the user; Sec. 4.4
@@ -414,6 +416,39 @@ AGILE_API int agile_device_view(agile_ctx *ctx, void *out, uint64_t size);
 /* For agile::launch_user: zero the context's per-launch state and number the launch, on
  * `stream`, right before a user launch. */
 AGILE_API int agile_run_reset(agile_ctx *ctx, void *stream);
+
+/* Validation of the Share Table (Sec. 3.4.1; needs cfg.share_slots > 0): one GPU thread
+ * runs the operations d_ops[4i .. 4i+3] = {op, page, a, b} one after the other --
+ * op 0: acquire `page` into user buffer a (the buffer d_bufs + a*4096; the page is
+ * copied from its cache line when cached, else read from the store into the buffer; an
+ * entry of the page already there is shared instead and its buffer returned), waiting
+ * for the fill; op 1: write 16 bytes of value b at byte offset a of the page's buffer
+ * and mark it modified; op 2: release the page (the last release of a modified buffer
+ * writes it into the page's cache line, which turns MODIFIED).  d_out[3i .. 3i+2] =
+ * {op 0: index of the buffer returned, op 2: 1 if this release wrote the buffer into the
+ * cache; the entry's state (0 none, 1 E, 2 S, 3 M, 4 O) and count afterwards}.  Served
+ * one at a time the table must decide as the sequential Share Table does.  The device
+ * side for user kernels is in agile_device.cuh. */
+AGILE_API int agile_share_replay(agile_ctx *ctx, const int32_t *d_ops, uint32_t n, void *d_bufs, int32_t *d_out,
+                                 void *stream);
+
+/* Lock-order checker (in place of the paper's debug lock chain, Sec. 3.5): a host-side
+ * analysis of a log of lock events.  Each blocking acquire of a lock while the thread
+ * holds others adds the order "held before acquired"; a try-acquire, which never
+ * waits, adds none.  An order that closes a cycle (including re-acquiring a held lock)
+ * is a way for threads to wait for each other forever.  Returns the number of acquires
+ * that closed a cycle (0: the order is consistent) or AGILE_EINVAL; the first cycle's
+ * locks go to cycle_out (up to cap), its length to *cycle_len (may be NULL). */
+#define AGILE_LOCK_ACQUIRE 0u
+#define AGILE_LOCK_RELEASE 1u
+#define AGILE_LOCK_TRY 2u
+typedef struct {
+  uint32_t thread;  /* who                                  */
+  uint32_t op;      /* AGILE_LOCK_ACQUIRE / _RELEASE / _TRY  */
+  uint64_t lock;    /* which lock                           */
+} agile_lock_event;
+AGILE_API int agile_lock_order_check(const agile_lock_event *ev, uint64_t n, uint64_t *cycle_out, uint32_t cap,
+                                     uint32_t *cycle_len);
 
 /* Synchronise the device and return the first error recorded on the GPU since the
  * last agile_check (0 if none), clearing it. */

@@ -47,6 +47,7 @@
 
 #include "agile.h"
 #include "agile_dev.cuh"
+#include "agile_share.cuh"
 
 namespace agile {
 namespace dev {
@@ -66,6 +67,29 @@ __device__ __forceinline__ bool copy_page(const Dev &d, const AppCtx &a, uint64_
 __device__ __forceinline__ bool prefetch(const Dev &d, const AppCtx &a, bool want, uint64_t page) {
   return api_prefetch(d, a, want, page);
 }
+
+// Share Table (Sec. 3.4.1; the context needs cfg.share_slots > 0), warp-collective.
+// share_acquire: lanes with `want` ask for `page` in their user buffer `mine` (4096
+//   bytes, 16-byte aligned).  If another user holds the page in a buffer, that buffer is
+//   shared (by pointer: *buf is it) and its count goes up; else `mine` is registered and
+//   filled from the cache or the store.  *tok: wait on it before reading *buf.  Returns
+//   0, AGILE_EAGAIN (table bucket full) or AGILE_ETIMEDOUT.
+// share_modified: the lane wrote into the shared buffer of `page`.
+// share_release: drop the lane's reference; the last one of a modified buffer writes it
+//   into the page's cache line (MODIFIED; the store gets it by write-back).  Returns 1
+//   when this lane did that, 0 when not, AGILE_ETIMEDOUT on a timeout.
+__device__ __forceinline__ int share_acquire(const Dev &d, const AppCtx &a, bool want, uint64_t page, void *mine,
+                                             uint8_t **buf, uint64_t *tok) {
+  return agile::share_acquire(d, a, want, page, (uint8_t *)mine, buf, tok);
+}
+__device__ __forceinline__ void share_modified(const Dev &d, bool want, uint64_t page) {
+  agile::share_modified(d, want, page);
+}
+__device__ __forceinline__ int share_release(const Dev &d, const AppCtx &a, bool want, uint64_t page) {
+  return agile::share_release(d, a, want, page);
+}
+// grid barrier over the launch's application warps (every one must call it)
+__device__ __forceinline__ bool barrier(const Dev &d, const AppCtx &a) { return app_barrier(d, a.n_warps, a.deadline); }
 
 }  // namespace dev
 

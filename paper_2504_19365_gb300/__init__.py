@@ -44,6 +44,7 @@ EXPORTED = [
     "agile_stats", "agile_reset_stats", "agile_check", "agile_launch_shape", "agile_strerror",
     "agile_config_parallelism", "agile_page_io", "agile_trace", "agile_link_probe", "agile_set_device_model",
     "agile_bfs_hbm", "agile_spmv_hbm", "agile_device_view", "agile_run_reset",
+    "agile_share_replay", "agile_lock_order_check",
 ]
 
 
@@ -70,6 +71,7 @@ class agile_config(C.Structure):
         ("cache_policy", C.c_uint32),
         ("emu_device_read_gbps", C.c_double),
         ("emu_device_write_gbps", C.c_double),
+        ("share_slots", C.c_uint32),
     ]
 
 
@@ -167,6 +169,8 @@ def lib():
             "agile_strerror": (C.c_char_p, [C.c_int]),
             "agile_page_io": (C.c_int, [vp, u64, u64, vp, vp, vp]),
             "agile_device_view": (C.c_int, [vp, vp, u64]),
+            "agile_share_replay": (C.c_int, [vp, vp, u32, vp, vp, vp]),
+            "agile_lock_order_check": (C.c_int, [vp, u64, vp, u32, C.POINTER(u32)]),
             "agile_run_reset": (C.c_int, [vp, vp]),
             "agile_bfs_hbm": (C.c_int, [vp, vp, vp, u32, u64, i32, vp, vp, vp]),
             "agile_spmv_hbm": (C.c_int, [vp, vp, vp, vp, u32, u32, u64, vp, vp, vp, vp]),
@@ -374,6 +378,28 @@ def agile_set_device_model(ctx, num_devices=1, emu_latency_ns=0, emu_queue_gbps=
                            emu_device_write_gbps=0.0) -> int:
     return _ok(lib().agile_set_device_model(ctx, num_devices, emu_latency_ns, emu_queue_gbps, emu_device_read_gbps,
                                             emu_device_write_gbps), "agile_set_device_model")
+
+
+AGILE_LOCK_ACQUIRE, AGILE_LOCK_RELEASE, AGILE_LOCK_TRY = 0, 1, 2
+
+
+class agile_lock_event(C.Structure):
+    _fields_ = [("thread", C.c_uint32), ("op", C.c_uint32), ("lock", C.c_uint64)]
+
+
+def agile_share_replay(ctx, d_ops, n, d_bufs, d_out, stream) -> int:
+    return _ok(lib().agile_share_replay(ctx, d_ops, n, d_bufs, d_out, stream), "agile_share_replay")
+
+
+def agile_lock_order_check(events):
+    """events: (thread, op, lock) triples.  Returns (cycles closed, first cycle's locks)."""
+    arr = (agile_lock_event * max(1, len(events)))(*[agile_lock_event(t, o, k) for t, o, k in events])
+    cyc = (C.c_uint64 * 64)()
+    ln = C.c_uint32()
+    r = lib().agile_lock_order_check(arr, len(events), cyc, 64, C.byref(ln))
+    if r < 0:
+        _ok(r, "agile_lock_order_check")
+    return r, [int(cyc[i]) for i in range(min(64, ln.value))]
 
 
 def agile_device_view(ctx, out_ptr, size) -> int:

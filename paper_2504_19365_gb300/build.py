@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INC = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libagile.so")
-SOURCES = ["agile_host.cu", "agile_apps.cu", "agile_train.cu", "agile_serve.cu"]
+SOURCES = ["agile_host.cu", "agile_apps.cu", "agile_train.cu", "agile_serve.cu", "agile_share.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -48,8 +48,9 @@ constexpr uint32_t kPolicyClock = 0, kPolicyFifo = 1;
 constexpr uint64_t SQE_EMPTY = 0, SQE_UPDATED = 1, SQE_ISSUED = 2;
 constexpr uint32_t OP_FLUSH = 0x00, OP_WRITE = 0x01, OP_READ = 0x02;
 
-// command context: what the completion of a command releases
-constexpr uint64_t CTX_NOP = 0, CTX_FILL = 1, CTX_WB = 2;
+// command context: what the completion of a command releases (CTX_BUF: a read into a
+// user buffer, which releases only the page's in-flight entry)
+constexpr uint64_t CTX_NOP = 0, CTX_FILL = 1, CTX_WB = 2, CTX_BUF = 3;
 __host__ __device__ __forceinline__ uint64_t ctx_make(uint64_t kind, uint32_t share_slot, uint32_t idx) {
   return (kind << 60) | ((uint64_t)(share_slot & 0x0FFFFFFFu) << 32) | idx;
 }
@@ -126,6 +127,11 @@ struct Dev {
   struct TraceRec *trace;
   uint32_t trace_cap;
   uint32_t *trace_n;
+  // Share Table of user buffers (Sec. 3.4.1): 4 slots per bucket; key = page + 1,
+  // buf = the buffer's address, meta = {state:8 | count:32 | closing:1}, tok = the token
+  // of the read that fills the buffer (0 while the entry is being set up)
+  unsigned long long *ub_key, *ub_buf, *ub_meta, *ub_tok;
+  uint32_t ub_mask;  // buckets - 1; ub_key == nullptr: no Share Table
   // backing devices: page p lives on device p mod ndev at block p / ndev; queue q
   // belongs to device q mod ndev (Sec. 4.3: requests interleaved over the SSDs)
   uint32_t ndev;
@@ -1100,6 +1106,8 @@ __device__ __forceinline__ void complete_command(const Dev &d, uint32_t q, uint3
     sh_remove(d, sh);
   } else if (kind == CTX_WB) {
     if (idx) atomicAnd(&d.tag[idx - 1], ~TAG_WB);  // flush write-back from the line itself
+    sh_remove(d, sh);
+  } else if (kind == CTX_BUF) {
     sh_remove(d, sh);
   }
   if (status) atomicAdd(stat_ptr(d, S_IO_ERRORS), 1ull);

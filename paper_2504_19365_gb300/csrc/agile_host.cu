@@ -529,6 +529,15 @@ int agile_init(const agile_config *cfg_in, agile_ctx **out) {
   d.ndev = cfg.num_devices;
   d.policy = cfg.cache_policy;
   d.dev_busy = (unsigned long long *)A((uint64_t)cfg.num_devices * 8);
+  if (cfg.share_slots) {
+    uint32_t ub = 256;  // buckets of 4 slots, at most half full
+    while ((uint64_t)ub * 2 < cfg.share_slots && ub < (1u << 30)) ub <<= 1;
+    d.ub_mask = ub - 1;
+    d.ub_key = (unsigned long long *)A((uint64_t)ub * 4 * 8);
+    d.ub_buf = (unsigned long long *)A((uint64_t)ub * 4 * 8);
+    d.ub_meta = (unsigned long long *)A((uint64_t)ub * 4 * 8);
+    d.ub_tok = (unsigned long long *)A((uint64_t)ub * 4 * 8);
+  }
   d.run = (RunState *)A(sizeof(RunState));
   d.stats = (unsigned long long *)A((size_t)kStatShards * S_COUNT * 8);
   d.err_sticky = (int32_t *)A(16);

@@ -74,3 +74,31 @@ def assert_cache_invariants(c: Ctx, store: np.ndarray | None = None):
         valid = page[sl][state[sl] != 0]
         assert len(valid) == len(set(valid.tolist())), f"duplicate tag in set {s}"
     return page, state
+
+
+def build_user_kernel(name: str):
+    """Compile tests/user_kernels/<name>.cu (a user kernel built against
+    include/agile_device.cuh) into tests/_build/lib<name>.so, linked to libagile.so, and
+    load it."""
+    import ctypes
+    import os
+    import subprocess
+
+    from paper_2504_19365_gb300 import build
+    here = os.path.dirname(os.path.abspath(__file__))
+    root = os.path.dirname(here)
+    lib = build.build()
+    pkg = os.path.dirname(lib)
+    src = os.path.join(here, "user_kernels", name + ".cu")
+    deps = [src, lib, os.path.join(root, "include", "agile_device.cuh")] + \
+        [os.path.join(pkg, "csrc", f) for f in os.listdir(os.path.join(pkg, "csrc"))]
+    out_dir = os.path.join(here, "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    so = os.path.join(out_dir, f"lib{name}.so")
+    if not os.path.exists(so) or os.path.getmtime(so) < max(os.path.getmtime(p) for p in deps):
+        cmd = [build.nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-shared",
+               "-Xcompiler", "-fPIC", "-I", os.path.join(root, "include"), "-I", os.path.join(pkg, "csrc"),
+               src, "-o", so + ".tmp", "-L", pkg, "-lagile", "-Xlinker", f"-rpath={pkg}"]
+        subprocess.run(cmd, check=True, capture_output=True, text=True)
+        os.replace(so + ".tmp", so)
+    return ctypes.CDLL(so)

@@ -10,9 +10,6 @@ bound, then use the data (Listing 1, Sec. 3.5; the transaction barrier of Sec. 3
     context, and a later launch finds the pages resident (the reads were drained).
 """
 import ctypes as C
-import os
-import subprocess
-
 import numpy as np
 import pytest
 
@@ -22,29 +19,14 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import paper_2504_19365_gb300 as ag  # noqa: E402
-from gpu_util import Ctx  # noqa: E402
+from gpu_util import Ctx, build_user_kernel  # noqa: E402
 
 DEV = "cuda:0"
-HERE = os.path.dirname(os.path.abspath(__file__))
-ROOT = os.path.dirname(HERE)
 
 
 @pytest.fixture(scope="module")
 def user_lib():
-    from paper_2504_19365_gb300 import build
-    lib = build.build()
-    src = os.path.join(HERE, "user_kernels", "token_demo.cu")
-    out_dir = os.path.join(HERE, "_build")
-    os.makedirs(out_dir, exist_ok=True)
-    so = os.path.join(out_dir, "libtoken_demo.so")
-    if not os.path.exists(so) or os.path.getmtime(so) < max(os.path.getmtime(src), os.path.getmtime(lib)):
-        pkg = os.path.dirname(lib)
-        cmd = [build.nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-shared",
-               "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", os.path.join(pkg, "csrc"),
-               src, "-o", so + ".tmp", "-L", pkg, "-lagile", "-Xlinker", f"-rpath={pkg}"]
-        subprocess.run(cmd, check=True, capture_output=True, text=True)
-        os.replace(so + ".tmp", so)
-    L = C.CDLL(so)
+    L = build_user_kernel("token_demo")
     L.token_demo.restype = C.c_int
     L.token_demo.argtypes = [C.c_void_p] * 6 + [C.c_uint64, C.c_uint32, C.c_void_p, C.c_uint32, C.c_void_p]
     return L
