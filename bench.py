@@ -534,12 +534,16 @@ def run_embedding(args, torch, ag, dev, rank, world):
 
 
 def fill_tables(ag, ctx, n_tables, rows, dim, stride, chunk_rows=1 << 20):
-    """Dyadic tables T_k[r, d] = ((r*131 + d*7 + k) mod 1024)/64 - 8 written in chunks."""
+    """Dyadic tables T_k[r, d] = ((r*131 + d*7 + k) mod 1024)/64 - 8 written in chunks (a
+    table's rows repeat with period 1024, so one 1024-row block is tiled)."""
     d = np.arange(dim, dtype=np.int64)[None, :]
     for k in range(n_tables):
+        r = np.arange(1024, dtype=np.int64)[:, None]
+        block = (((r * 131 + d * 7 + k) % 1024).astype(np.float32) / np.float32(64.0) - np.float32(8.0))
+        big = np.ascontiguousarray(np.tile(block, (chunk_rows // 1024 + 1, 1)))
         for r0 in range(0, rows, chunk_rows):
-            r = np.arange(r0, min(rows, r0 + chunk_rows), dtype=np.int64)[:, None]
-            blk = (((r * 131 + d * 7 + k) % 1024).astype(np.float32) / np.float32(64.0) - np.float32(8.0))
+            m = min(chunk_rows, rows - r0)
+            blk = np.ascontiguousarray(big[r0 % 1024:r0 % 1024 + m])
             ag.agile_store_write(ctx, k * stride + r0 * dim * 4, blk.ctypes.data, blk.nbytes)
 
 

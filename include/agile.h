@@ -310,9 +310,11 @@ AGILE_API int agile_bfs_noalloc(agile_ctx *ctx, uint64_t offsets_byte0, uint64_t
 /* Serving loop: continuous batching of lookup requests (serving extension of the
  * Sec. 4.4 lookups).  agile_serve_start launches one long-running call on `stream`
  * that keeps the queues, the emulated device and the cache resident for up to
- * session_ns (0 = 60 s); requests submitted meanwhile are admitted when the free
- * cache-line and queue-slot budget covers them and are served alongside the requests
- * already running.  A request is one sum-pooled embedding bag exactly as computed by
+ * session_ns (0 = 60 s); requests submitted meanwhile are admitted, oldest first, when
+ * the free cache-line budget (half of the cache's lines; a request holds one line per
+ * index + 1, at most the budget) covers them, or when nothing else runs, and are
+ * served alongside the requests already running.  Queue slots need no budget: each is
+ * returned by its completion, and a full queue sends a request to the next queue.  A request is one sum-pooled embedding bag exactly as computed by
  * agile_embedding_bag (same result alone or in any mix); its device buffers must be
  * written before it is submitted and left alone until it completes; dim <= 128.
  * While a session runs its kernel occupies every SM: launch no other kernel on the

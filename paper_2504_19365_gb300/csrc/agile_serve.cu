@@ -4,8 +4,11 @@
 //   - the host writes request descriptors into a ring in mapped pinned memory and
 //     publishes each one by its sequence number (release); it never launches work;
 //   - application warp 0 is the scheduler: it reads the ring (system-scope acquire) and
-//     admits a request once the free cache-line and queue-slot budget covers it (a
-//     request needs at most one line per index and one slot per missing page);
+//     admits a request, oldest first, once the free cache-line budget (half of the
+//     cache's lines) covers the lines it may hold (its indices + 1, at most the budget),
+//     or when nothing else is running.  Queue slots need no budget of their own: a
+//     request takes at most one slot per missing page, every slot comes back with its
+//     completion, and a full queue only sends the issuing warp to the next queue;
 //   - every other application warp takes bags from the oldest admitted request that
 //     still has unclaimed bags (a shared cursor moves past fully claimed requests), so
 //     requests that arrive while others run are served alongside them;

@@ -102,3 +102,23 @@ def build_user_kernel(name: str):
         subprocess.run(cmd, check=True, capture_output=True, text=True)
         os.replace(so + ".tmp", so)
     return ctypes.CDLL(so)
+
+
+def dyadic_rows(k: int, r: np.ndarray, dim: int) -> np.ndarray:
+    """Rows r of dyadic table k: T_k[r, d] = ((r*131 + d*7 + k) mod 1024) / 64 - 8, so that
+    every FP32 sum of up to 2^16 of them is exact (any order gives the same bits)."""
+    d = np.arange(dim, dtype=np.int64)[None, :]
+    r = np.asarray(r, dtype=np.int64)[:, None]
+    return (((r * 131 + d * 7 + k) % 1024).astype(np.float32) / np.float32(64.0) - np.float32(8.0))
+
+
+def fill_dyadic(c: "Ctx", n_tables: int, rows: int, dim: int, stride: int, chunk_rows: int = 1 << 20):
+    """Write n_tables dyadic tables (table k at byte k*stride of the store).  A table's
+    rows repeat with period 1024, so one 1024-row block is tiled."""
+    for k in range(n_tables):
+        block = dyadic_rows(k, np.arange(1024), dim)
+        big = np.tile(block, (chunk_rows // 1024 + 1, 1))
+        for r0 in range(0, rows, chunk_rows):
+            m = min(chunk_rows, rows - r0)
+            s = r0 % 1024
+            c.put(k * stride + r0 * dim * 4, big[s:s + m])
