@@ -1045,6 +1045,22 @@ def run_hits(args, torch, ag, dev):
             flush.zero_()
             ms += timed(torch, lambda: torch.nn.functional.embedding_bag(idx, T, off[:-1], mode="sum"))
         res["torch_embedding_bag_hbm_lookups_per_s"] = nb * pool / (ms / args.steps * 1e-3)
+        # the plain-gather ceiling: the library's embedding bag over the same table in HBM,
+        # without the cache (same warps-per-bag layout, same summation order)
+        for _ in range(3):
+            ag.agile_embedding_bag_hbm(ctx, T.data_ptr(), rows, dim, idx.data_ptr(), off.data_ptr(), nb,
+                                       out.data_ptr(), stream)
+        ms = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            ms += timed(torch, lambda: ag.agile_embedding_bag_hbm(ctx, T.data_ptr(), rows, dim, idx.data_ptr(),
+                                                                  off.data_ptr(), nb, out.data_ptr(), stream))
+        t = ms / args.steps * 1e-3
+        algo = nb * pool * (dim * 4 + 8) + (nb + 1) * 8 + nb * dim * 4
+        res["hbm_gather"] = {"lookups_per_s": nb * pool / t, "ms_per_launch": t * 1e3,
+                             "roofline": {"bound": "hbm", "achieved": algo / t / 1e9, "peak": HBM_PEAK, "unit": "GB/s",
+                                          "frac": algo / t / 1e9 / HBM_PEAK, "kernel": "hbm_bag_kernel<1>"},
+                             "what": "agile_embedding_bag_hbm: the same bags over the table in HBM, no cache"}
         del T
         res["workload"] = "65,536 bags x 16 uniform lookups, 2,097,152 x 128 FP32 table (1 GiB) fully cached (all hits)"
     finally:

@@ -115,7 +115,11 @@ typedef struct {
   double emu_device_write_gbps;  /* per-device write throughput cap, GB/s (0 = none) */
   uint32_t share_slots;     /* Share Table entries for user buffers (Sec. 3.4.1); 0 = no
                                Share Table (it is an option, as in the paper)        */
+  uint32_t emu_extra_engines; /* application warps a call leaves idle that also serve the
+                               emulated device, at most: 0 = one per CTA of the launch,
+                               AGILE_NO_EXTRA_ENGINES = none (only warp 0 of each CTA) */
 } agile_config;
+#define AGILE_NO_EXTRA_ENGINES 0xFFFFFFFFu
 
 /* Replacement policies of the cache (Sec. 3.4 leaves the policy to the user; Sec. 4.4
  * uses clock).  Both pick a victim within the page's set starting at the set's hand and
@@ -268,6 +272,16 @@ AGILE_API int agile_spmv(agile_ctx *ctx, uint64_t offsets_byte0, uint64_t cols_b
                          uint32_t n_rows, uint32_t n_cols, const float *d_x, float *d_y,
                          uint64_t *d_entries, uint32_t mode, void *stream);
 
+/* The embedding bag of agile_embedding_bag over a table held in device memory of the
+ * caller (d_table: rows x dim floats, 16-byte aligned), without the cache or the queues:
+ * the hit path's ceiling (plain gathers of the same rows in the same order; the same
+ * bits) and the "kernel time" step of a breakdown like Sec. 4.5's.  A warp per bag;
+ * indices outside [0, rows) read row 0 and record AGILE_EINVAL (agile_check).  Uses
+ * the context only for its device and error word. */
+AGILE_API int agile_embedding_bag_hbm(agile_ctx *ctx, const float *d_table, uint32_t rows, uint32_t dim,
+                                      const int64_t *d_idx, const int64_t *d_offsets, uint32_t n_bags,
+                                      float *d_out, void *stream);
+
 /* Step 1 of the Sec. 4.5 three-step breakdown ("kernel time": the application kernel
  * with the graph in HBM, read with plain loads): the BFS of agile_bfs, the same kernel
  * and launch, over a CSR held in device memory of the caller instead of the store --
@@ -393,7 +407,9 @@ typedef struct {
   uint32_t q, cid, opcode, status;  /* queue, command id, 0 flush/no-op 1 write 2 read,
                                        NVMe status (bit 16: completion dropped by the
                                        fault injector)                                  */
-  uint32_t pad[4];
+  uint64_t t_commit; /* the command was written to its submission slot (carried in the
+                        command's reserved dwords 2-3)                                  */
+  uint32_t pad[2];
 } agile_trace_rec;
 
 /* Copy the device's command trace (cfg.trace_records > 0) to host: up to `cap` records

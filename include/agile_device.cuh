@@ -106,6 +106,7 @@ int launch_user(agile_ctx *ctx, const App &app, void *stream, uint32_t app_warps
       per_sm <= 0)
     return AGILE_ECUDA;
   d.app_active = app_warps;
+  if (d.extra_engines == 0xFFFFFFFFu) d.extra_engines = (uint32_t)(per_sm * sms);  // default: one per CTA
   r = agile_run_reset(ctx, stream);
   if (r) return r;
   App a = app;

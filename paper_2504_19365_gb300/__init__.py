@@ -32,6 +32,7 @@ AGILE_FAULT_DROP_CQE = 2
 AGILE_TOKEN_HIT = (1 << 64) - 1
 AGILE_POLICY_CLOCK = 0
 AGILE_POLICY_FIFO = 1
+AGILE_NO_EXTRA_ENGINES = 0xFFFFFFFF
 
 EXPORTED = [
     "agile_config_default", "agile_init", "agile_destroy", "agile_store_write",
@@ -44,7 +45,7 @@ EXPORTED = [
     "agile_stats", "agile_reset_stats", "agile_check", "agile_launch_shape", "agile_strerror",
     "agile_config_parallelism", "agile_page_io", "agile_trace", "agile_link_probe", "agile_set_device_model",
     "agile_bfs_hbm", "agile_spmv_hbm", "agile_device_view", "agile_run_reset",
-    "agile_share_replay", "agile_lock_order_check",
+    "agile_share_replay", "agile_lock_order_check", "agile_embedding_bag_hbm",
 ]
 
 
@@ -72,6 +73,7 @@ class agile_config(C.Structure):
         ("emu_device_read_gbps", C.c_double),
         ("emu_device_write_gbps", C.c_double),
         ("share_slots", C.c_uint32),
+        ("emu_extra_engines", C.c_uint32),
     ]
 
 
@@ -85,7 +87,8 @@ class agile_trace_rec(C.Structure):
         ("cid", C.c_uint32),
         ("opcode", C.c_uint32),
         ("status", C.c_uint32),
-        ("pad", C.c_uint32 * 4),
+        ("t_commit", C.c_uint64),
+        ("pad", C.c_uint32 * 2),
     ]
 
 
@@ -173,6 +176,7 @@ def lib():
             "agile_lock_order_check": (C.c_int, [vp, u64, vp, u32, C.POINTER(u32)]),
             "agile_run_reset": (C.c_int, [vp, vp]),
             "agile_bfs_hbm": (C.c_int, [vp, vp, vp, u32, u64, i32, vp, vp, vp]),
+            "agile_embedding_bag_hbm": (C.c_int, [vp, vp, u32, u32, vp, vp, u32, vp, vp]),
             "agile_spmv_hbm": (C.c_int, [vp, vp, vp, vp, u32, u32, u64, vp, vp, vp, vp]),
             "agile_set_device_model": (C.c_int, [vp, u32, u32, C.c_double, C.c_double, C.c_double]),
             "agile_trace": (C.c_int, [vp, vp, u32, C.POINTER(u32)]),
@@ -279,6 +283,12 @@ def agile_spmv(ctx, offsets_byte0, cols_byte0, vals_byte0, n_rows, n_cols, d_x, 
                stream) -> int:
     return _ok(lib().agile_spmv(ctx, offsets_byte0, cols_byte0, vals_byte0, n_rows, n_cols, d_x, d_y, d_entries,
                                 mode, stream), "agile_spmv")
+
+
+def agile_embedding_bag_hbm(ctx, d_table, rows, dim, d_idx, d_offsets, n_bags, d_out, stream) -> int:
+    """Embedding bag over a table in device memory, no cache (the hit path's ceiling)."""
+    return _ok(lib().agile_embedding_bag_hbm(ctx, d_table, rows, dim, d_idx, d_offsets, n_bags, d_out, stream),
+               "agile_embedding_bag_hbm")
 
 
 def agile_bfs_hbm(ctx, d_offsets, d_cols, n_vertices, n_cols, src, d_level, d_edges, stream) -> int:
@@ -422,7 +432,7 @@ def agile_page_io(ctx, page0: int, n: int):
 
 
 TRACE_DTYPE = [("page", "<u8"), ("t_seen", "<u8"), ("t_start", "<u8"), ("t_done", "<u8"), ("q", "<u4"),
-               ("cid", "<u4"), ("opcode", "<u4"), ("status", "<u4"), ("pad", "<u4", (4,))]
+               ("cid", "<u4"), ("opcode", "<u4"), ("status", "<u4"), ("t_commit", "<u8"), ("pad", "<u4", (2,))]
 
 
 def agile_trace(ctx, cap: int):

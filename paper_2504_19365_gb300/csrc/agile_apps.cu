@@ -1203,6 +1203,72 @@ struct SpmvAppT {
 
 using SpmvApp = SpmvAppT<false>;
 
+// ============================================================================ plain HBM gather
+// The embedding bag over a table held in HBM, without the cache or the queues: the hit
+// path's ceiling and the "kernel time" of its breakdown.  A warp per bag (bags
+// b, b + W, ...); lane l adds the float4 columns l, l + 32, ... of the bag's rows in
+// increasing index order (FP32, no fusion: the cached path's bits).  The rows of up to
+// 32 indices are loaded before the first add, and the next bag's indices are read while
+// they fly.
+template <int MF4>
+__global__ void __launch_bounds__(256) hbm_bag_kernel(const float *table, uint32_t rows, uint32_t dim,
+                                                      const int64_t *idx, const int64_t *off, uint32_t n_bags,
+                                                      float *out, int32_t *err) {
+  const unsigned l = threadIdx.x & 31;
+  const uint32_t nf4 = dim / 4;
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  constexpr int RB = MF4 >= 4 ? 4 : 16 / MF4;  // rows whose loads are in flight together
+  for (uint64_t b = warp; b < n_bags; b += nw) {
+    int64_t s = off[b], e = off[b + 1];
+    float4 acc[MF4];
+#pragma unroll
+    for (int c = 0; c < MF4; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t i0 = s; i0 < e; i0 += 32) {
+      int64_t i = i0 + l;
+      uint64_t r = i < e ? (uint64_t)__ldg(&idx[i]) : 0;
+      if (i < e && r >= rows) {
+        atomicCAS(err, 0, 22);
+        r = 0;
+      }
+      uint32_t cnt = (uint32_t)min((int64_t)32, e - i0);
+      for (uint32_t j0 = 0; j0 < cnt; j0 += RB) {
+        float4 v[RB][MF4];
+#pragma unroll
+        for (int jj = 0; jj < RB; ++jj) {
+          uint64_t rj = __shfl_sync(kFull, r, (j0 + jj) & 31);
+          const float4 *row = (const float4 *)(table + rj * dim);
+#pragma unroll
+          for (int c = 0; c < MF4; ++c) {
+            uint32_t col = l + 32 * c;
+            v[jj][c] = (j0 + jj < cnt && col < nf4) ? __ldg(row + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        }
+#pragma unroll
+        for (int jj = 0; jj < RB; ++jj) {
+          if (j0 + jj < cnt) {
+#pragma unroll
+            for (int c = 0; c < MF4; ++c) {
+              acc[c].x = __fadd_rn(acc[c].x, v[jj][c].x);
+              acc[c].y = __fadd_rn(acc[c].y, v[jj][c].y);
+              acc[c].z = __fadd_rn(acc[c].z, v[jj][c].z);
+              acc[c].w = __fadd_rn(acc[c].w, v[jj][c].w);
+            }
+          }
+        }
+      }
+    }
+    float4 *o = (float4 *)(out + b * dim);
+#pragma unroll
+    for (int c = 0; c < MF4; ++c)
+      if (l + 32 * c < nf4) o[l + 32 * c] = acc[c];
+  }
+}
+
+__global__ void hbm_bag_err_kernel(Dev d, const int32_t *err) {
+  if (threadIdx.x == 0 && *err) set_error(d, -(*err));
+}
+
 __global__ void bfs_init_kernel(int32_t *level, uint32_t *vis, uint32_t n, int32_t src) {
   uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (i < n) level[i] = (i == (uint64_t)src) ? 0 : -1;
@@ -1426,6 +1492,36 @@ int agile_bfs_noalloc(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0,
   if (r) return r;
   return bfs_launch(c, offsets_byte0, cols_byte0, n_vertices, src, d_level, d_edges_scanned, mode, stream,
                     scratch, kNoAllocHubMax, vis);
+}
+
+int agile_embedding_bag_hbm(agile_ctx *c, const float *d_table, uint32_t rows, uint32_t dim, const int64_t *d_idx,
+                            const int64_t *d_offsets, uint32_t n_bags, float *d_out, void *stream) {
+  if (!c) return AGILE_EINVAL;
+  if (n_bags == 0) return AGILE_OK;
+  if (!d_table || !d_idx || !d_offsets || !d_out) return AGILE_EINVAL;
+  if (dim == 0 || dim % 4 || dim > 32 * 4 * kMaxF4) return AGILE_EINVAL;
+  if ((((uintptr_t)d_out) | ((uintptr_t)d_table)) & 15) return AGILE_EINVAL;
+  AGILE_CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t s = as_stream(stream);
+  // the error word lives in the context's per-launch state (flag[0]), which no launch
+  // on this stream uses at the same time
+  int32_t *err = (int32_t *)&c->dev.run->flag[0];
+  AGILE_CUDA_TRY(cudaMemsetAsync(err, 0, 4, s));
+  int per_sm = 0;
+  uint32_t grid;
+  auto launch = [&](auto kern) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+    grid = (uint32_t)std::max(1, per_sm) * (uint32_t)c->sms;
+    grid = (uint32_t)std::min<uint64_t>(grid, ((uint64_t)n_bags + 7) / 8);
+    kern<<<grid, 256, 0, s>>>(d_table, rows, dim, d_idx, d_offsets, n_bags, d_out, err);
+  };
+  if (dim <= 128) launch(hbm_bag_kernel<1>);
+  else if (dim <= 256) launch(hbm_bag_kernel<2>);
+  else launch(hbm_bag_kernel<kMaxF4>);
+  AGILE_CUDA_TRY(cudaGetLastError());
+  hbm_bag_err_kernel<<<1, 32, 0, s>>>(c->dev, err);
+  AGILE_CUDA_TRY(cudaGetLastError());
+  return AGILE_OK;
 }
 
 int agile_bfs_hbm(agile_ctx *c, const int64_t *d_offsets, const int32_t *d_cols, uint32_t n_vertices,

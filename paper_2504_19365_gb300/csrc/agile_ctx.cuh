@@ -98,6 +98,7 @@ int launch_engine(agile_ctx *c, const App &app, void *stream, uint32_t active = 
   AGILE_CUDA_TRY(cudaGetLastError());
   Dev d = c->dev;
   d.app_active = c->cfg.app_warps ? c->cfg.app_warps : active;
+  if (d.extra_engines == 0xFFFFFFFFu) d.extra_engines = (uint32_t)grid;  // default: one per CTA
   App a = app;
   void *args[] = {(void *)&d, (void *)&a};
   AGILE_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)engine_kernel<App>, dim3(grid), dim3(kThreads),

@@ -89,7 +89,8 @@ struct TraceRec {
   unsigned long long t_start; // taken by an engine: data movement starts
   unsigned long long t_done;  // completion entry posted
   uint32_t q, cid, opcode, status;
-  uint32_t pad[4];
+  unsigned long long t_commit;  // the command was written to its submission slot
+  uint32_t pad[2];
 };
 
 struct Dev {
@@ -150,6 +151,7 @@ struct Dev {
   uint32_t prefetch_depth;
   int32_t *err_sticky;  // first error since the last agile_check
   uint32_t app_active;  // application warps that take part in this launch (0 = all)
+  uint32_t extra_engines;  // idle application warps that may also serve the device
   uint64_t session_ns;  // length of a long-running launch (serving loop); 0 = timeout_ns
 };
 
@@ -364,7 +366,9 @@ __device__ __forceinline__ void sq_commit(const Dev &d, uint32_t q, uint32_t slo
   uint64_t i = (uint64_t)q * d.depth + slot;
   uint32_t *e = d.sq[i].dw;
   uint64_t slba = block_of_page(d, page) * (kPage / 512);
-  int4 a = make_int4((int)(opcode | (slot << 16)), 1, 0, 0);                      // dw0-3
+  // dw2-3 (reserved in NVMe) carry the commit time for the device's trace
+  uint64_t now = gtimer();
+  int4 a = make_int4((int)(opcode | (slot << 16)), 1, (int)(uint32_t)now, (int)(uint32_t)(now >> 32));  // dw0-3
   int4 b = make_int4(0, 0, (int)(uint32_t)prp1, (int)(uint32_t)(prp1 >> 32));      // dw4-7
   int4 c = make_int4(0, 0, (int)(uint32_t)slba, (int)(uint32_t)(slba >> 32));      // dw8-11
   int4 f = make_int4((int)(kPage / 512 - 1), 0, 0, 0);                             // dw12-15
@@ -1272,13 +1276,14 @@ static __device__ uint32_t emu_serve(const Dev &d, uint32_t q) {
   __syncwarp();  // lane 0's acquire of the doorbell orders the SQE reads of every lane
   // command fields: lane i < k reads SQE f+i
   uint32_t dw0 = 0, nlb = 0, status = 0;
-  uint64_t prp1 = 0, slba = 0;
+  uint64_t prp1 = 0, slba = 0, t_commit = 0;
   bool drop = false;
   if (l < k) {
     uint64_t i = (uint64_t)q * d.depth + ((f + l) & d.dmask);
     const uint32_t *e = d.sq[i].dw;
     int4 a = ld_cg16(e), b = ld_cg16(e + 4), c = ld_cg16(e + 8), g = ld_cg16(e + 12);
     dw0 = (uint32_t)a.x;
+    t_commit = (uint64_t)(uint32_t)a.z | ((uint64_t)(uint32_t)a.w << 32);
     prp1 = (uint64_t)(uint32_t)b.z | ((uint64_t)(uint32_t)b.w << 32);
     slba = (uint64_t)(uint32_t)c.z | ((uint64_t)(uint32_t)c.w << 32);
     nlb = (uint32_t)g.x & 0xFFFFu;
@@ -1356,6 +1361,7 @@ static __device__ uint32_t emu_serve(const Dev &d, uint32_t q) {
         tr->cid = cid;
         tr->opcode = dw0 & 0xFFu;
         tr->status = status | (drop ? 0x10000u : 0u);
+        tr->t_commit = t_commit;
       }
     }
     if (drop) {
@@ -1384,8 +1390,9 @@ static __device__ uint32_t emu_serve(const Dev &d, uint32_t q) {
 // q = cta, cta + grid, ...  The other warps run the application.  No kernel of the
 // library ever waits on another launch: the device, the pollers and the waiters are
 // co-resident warps of one grid, and every wait is bounded by a deadline.
-static __device__ void service_loop(const Dev &d, uint32_t n_app, uint64_t deadline, bool poll) {
-  uint32_t sw = blockIdx.x, nsw = gridDim.x;
+// `sw` of `nsw`: this engine's number among the launch's engines (rotation start).
+static __device__ void service_loop(const Dev &d, uint32_t n_app, uint64_t deadline, bool poll, uint32_t sw,
+                                    uint32_t nsw) {
   unsigned l = lane_id();
   uint32_t ns = 32;
   uint32_t windows = (d.Q + 31) / 32;
@@ -1523,16 +1530,27 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<App>::value) engine_kernel
   // queue each, and the service warps only serve the device
   const bool pollers = n_app - n_active >= d.Q;
   if (warp == 0) {
-    service_loop(d, n_app, deadline + d.timeout_ns, !pollers);
+    uint32_t idle = n_app - n_active, q_used = pollers ? d.Q : 0;
+    uint32_t extra = idle > q_used ? min(idle - q_used, d.extra_engines) : 0;
+    service_loop(d, n_app, deadline + d.timeout_ns, !pollers, blockIdx.x, gridDim.x + extra);
     return;
   }
   AppCtx a;
   a.warp = blockIdx.x * (kWarps - 1) + (warp - 1);
   a.n_warps = n_active;
   if (a.warp >= a.n_warps) {
-    // not needed by this call: keeps the working set of the active warps in the cache
+    // not needed by this call: keeps the working set of the active warps in the cache.
+    // The first Q such warps poll a completion queue each (when there are Q of them),
+    // the next ones (up to d.extra_engines) serve the device as additional engines.
     if (lane_id() == 0) atomicAdd(&d.run->app_done, 1u);
-    if (pollers && a.warp - a.n_warps < d.Q) poller_loop(d, a.warp - a.n_warps, n_app, deadline + d.timeout_ns);
+    uint32_t idle = a.warp - a.n_warps, q_used = pollers ? d.Q : 0;
+    if (idle < q_used) {
+      poller_loop(d, idle, n_app, deadline + d.timeout_ns);
+    } else {
+      uint32_t extra = min(n_app - n_active - q_used, d.extra_engines);
+      if (idle - q_used < extra)
+        service_loop(d, n_app, deadline + d.timeout_ns, false, gridDim.x + (idle - q_used), gridDim.x + extra);
+    }
     return;
   }
   // home queue by thread index, spread so that the lanes of a warp and the lane 0 of

@@ -562,6 +562,9 @@ int agile_init(const agile_config *cfg_in, agile_ctx **out) {
   d.fault_thresh = (uint32_t)fmin(4294967295.0, cfg.fault_rate * 4294967296.0);
   d.seed = cfg.seed;
   d.timeout_ns = cfg.wait_timeout_ns;
+  d.extra_engines = cfg.emu_extra_engines == AGILE_NO_EXTRA_ENGINES
+                        ? 0u
+                        : (cfg.emu_extra_engines ? cfg.emu_extra_engines : 0xFFFFFFFFu);
   d.prefetch_depth = cfg.prefetch_depth;
   if (cudaDeviceSynchronize() != cudaSuccess) {
     agile_destroy(c);

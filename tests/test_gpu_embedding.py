@@ -127,3 +127,24 @@ def test_large_cache_cold_then_warm_hits(app_warps):
             # every looked-up row was served by a probe of its own or of a warp-mate
             assert st["hits"] + st["warp_coalesced"] >= int(off[-1])
         assert_cache_invariants(c)
+
+
+@pytest.mark.parametrize("dim", [16, 128, 512])
+def test_hbm_gather_ceiling_equals_oracle(dim):
+    # the hit path's plain-gather ceiling (table in HBM, no cache) computes the same bits
+    rows, nb = 5000, 700
+    T = synth.table_normal(21, rows, dim)
+    lens = synth.uniform_int(22, nb, 40)           # 0-39 indices a bag, empty bags included
+    off = np.zeros(nb + 1, dtype=np.int64)
+    off[1:] = np.cumsum(lens)
+    idx = synth.indices_uniform(23, int(off[-1]), rows)
+    with Ctx(4096 * 16, cache_bytes=8 * 4096, ways=8, num_queues=4, queue_depth=64) as c:
+        d_t = torch.from_numpy(T).to(DEV)
+        d_idx, d_off = torch.from_numpy(idx).to(DEV), torch.from_numpy(off).to(DEV)
+        out = torch.full((nb, dim), float("nan"), dtype=torch.float32, device=DEV)
+        ag.agile_embedding_bag_hbm(c.h, d_t.data_ptr(), rows, dim, d_idx.data_ptr(), d_off.data_ptr(), nb,
+                                   out.data_ptr(), c.stream)
+        torch.cuda.synchronize()
+        c.check()
+        want = oracle.embedding_bag(T, idx, off)
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), want.view(np.uint32))
