@@ -410,6 +410,8 @@ def run_bfs(args, torch, ag, dev, rank, world):
     # the same BFS with the SSD-like device model (outside the headline)
     try:
         ag.agile_set_device_model(ctx, **SSD_MODEL)
+        one(srcs[0], ag.AGILE_ASYNC)
+        check_or_raise(ag, ctx)
         steps(ag.AGILE_ASYNC, 1)
         ms_sa, w_sa = steps(ag.AGILE_ASYNC, 2)
         ms_ss, w_ss = steps(ag.AGILE_SYNC, 2)
@@ -516,6 +518,8 @@ def run_embedding(args, torch, ag, dev, rank, world):
         both(args.warmup)
         ta, ts = both(max(5, args.steps))
         ag.agile_set_device_model(ctx, **SSD_MODEL)
+        step(ag.AGILE_SYNC)
+        check_or_raise(ag, ctx)
         both(1)
         sa, ss = both(5)
         ag.agile_set_device_model(ctx)
@@ -565,6 +569,14 @@ SSD_MODEL = {"num_devices": 4, "emu_latency_ns": 80_000, "emu_queue_gbps": 0.0, 
 SSD_DESC = "4 emulated SSDs, 3.7 GB/s read and 2.2 GB/s write each, 80 us per command, 128 x 256 queues"
 
 
+def check_or_raise(ag, ctx):
+    """Stop a leg at its first device error (a timed-out call takes the whole wait bound;
+    repeating it would only repeat the wait)."""
+    err = ag.agile_check(ctx)
+    if err:
+        raise RuntimeError(f"device error: {ag.strerror(err)}")
+
+
 def overlap_sweep(torch, ag, dev, ctx, stride, nt, rows, dim, nbags, pool, stream, flush, batches_full=4, reps=5):
     """Config-3 overlap sweep on an open context: per batch the lookups of nt tables x
     nbags bags x pooling, then the FP32 compute phase sized to r x the sync I/O time
@@ -587,6 +599,7 @@ def overlap_sweep(torch, ag, dev, ctx, stride, nt, rows, dim, nbags, pool, strea
                 ctx, 0, stride, nt, rows, dim, d_idx.data_ptr(), pool, nbags, batches, iters, out.data_ptr(),
                 mode, stream))
         go(ag.AGILE_SYNC, 0)
+        check_or_raise(ag, ctx)
         t_io = statistics.median(go(ag.AGILE_SYNC, 0) for _ in range(3))
         t_io_async = statistics.median(go(ag.AGILE_ASYNC, 0) for _ in range(3))
         # compute cost per iteration on a warm cache (this batch set fits in it)
@@ -638,6 +651,8 @@ def run_dlrm(args, torch, ag, dev):
             res["overlap_ssd"] = overlap_sweep(torch, ag, dev, ctx, stride, nt, rows, dim, nbags, pool, stream,
                                                flush, batches_full=2)
             res["overlap_ssd"]["device"] = SSD_DESC
+        except Exception as e:  # noqa: BLE001
+            res["overlap_ssd"] = {"error": f"{type(e).__name__}: {e}"}
         finally:
             ag.agile_set_device_model(ctx)
         res["serving"] = run_serving(torch, ag, dev, ctx, nt, rows, dim, stride, stream)
@@ -857,7 +872,9 @@ def run_pages(args, torch, ag, dev, link_peak):
                     flush.zero_()
                     t = timed(torch, lambda: ag.agile_read_async(ctx, d_pages.data_ptr(), pages.size, dst.data_ptr(),
                                                                  0, mode, stream))
-                    if i:
+                    if i == 0:
+                        check_or_raise(ag, ctx)
+                    else:
                         ts.append(t)
                 ms = statistics.median(ts)
                 gbs = pages.size * 4096 / (ms * 1e-3) / 1e9
@@ -1118,6 +1135,7 @@ def main():
                     res[name] = {"error": f"{type(e).__name__}: {e}"}
                 if isinstance(res[name], dict):
                     res[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+                print(f"[bench] {name}: {time.perf_counter() - t0:.1f} s", file=sys.stderr, flush=True)
 
             def spmv():
                 r = run_spmv(args, torch, ag, dev, graph[0], graph[1])

@@ -522,12 +522,28 @@ struct BfsAppT {
   // most (column entries) / kHub slices, which the queue holds; should a reservation
   // still run past the queue's end, its records inside the queue are published empty
   // and the lanes scan their lists here.  False for a lane that keeps its list.
+  // Slices of the list [s, e) (at least kHub entries) follow the 2-page grid of the
+  // column array, so that no page is shared by two slices of one list: slice 0 ends at
+  // the first multiple of kSlice entries at least kHub entries past s, the following
+  // ones hold kSlice entries, and a last piece of fewer than kHub entries joins the slice
+  // before it.  Every slice holds at least kHub entries (so a level needs at most
+  // entries / kHub records) and fewer than kSlice + 2 kHub.
+  __device__ __forceinline__ static int64_t slice_b1(int64_t s) {
+    return (s + kHub + kSlice - 1) / kSlice * kSlice;
+  }
+  __device__ __forceinline__ static uint32_t slice_count(int64_t s, int64_t e) {
+    int64_t b1 = slice_b1(s);
+    if (b1 >= e) return 1;
+    int64_t rest = e - b1;
+    uint32_t full = (uint32_t)(rest / kSlice);
+    return 1 + full + ((rest % kSlice) >= kHub ? 1 : 0);
+  }
   __device__ bool push_hub(const Dev &d, uint32_t deg, int64_t s, int64_t e, int32_t L) const {
     unsigned l = lane_id();
     bool hub = deg >= kHub;
     unsigned hm = __ballot_sync(kFull, hub);
     if (!hm) return false;
-    uint32_t sl = hub ? (deg + kSlice - 1) / kSlice : 0;
+    uint32_t sl = hub ? slice_count(s, e) : 0;
     uint32_t incl = sl;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -551,11 +567,11 @@ struct BfsAppT {
       int h = __ffs(m) - 1;
       int64_t sh = __shfl_sync(kFull, s, h), eh = __shfl_sync(kFull, e, h);
       uint32_t bh = base + __shfl_sync(kFull, excl, h), nh = __shfl_sync(kFull, sl, h);
+      const int64_t b1 = slice_b1(sh);
       for (uint32_t j = l; j < nh; j += 32) {
         HubEntry *r = &hubq[bh + j];
-        int64_t p0 = sh + (int64_t)j * kSlice;
-        r->p0 = p0;
-        r->p1 = min(eh, p0 + (int64_t)kSlice);
+        r->p0 = j == 0 ? sh : b1 + (int64_t)(j - 1) * kSlice;
+        r->p1 = j + 1 == nh ? eh : b1 + (int64_t)j * kSlice;
         st_rel64(&r->ready, t);
       }
     }
@@ -599,6 +615,51 @@ struct BfsAppT {
       visit_n<2>(act, u, L, found);
     }
     return true;
+  }
+
+  // ASYNC, sparse chunks: the offsets of the chunk's frontier vertices are read, then the
+  // column pages of their short lists are requested together, without waiting, before
+  // the chunk's units are scanned -- so the misses of up to kChunk / 32 units overlap
+  // instead of following one another.  Only when each lane has at most one page to
+  // request (sparse levels): in dense ones the pages would outnumber what the cache
+  // holds for the running warps.
+  __device__ bool prefetch_chunk(const Dev &d, const AppCtx &a, uint32_t c0, int32_t L, Pin &pc) const {
+    constexpr int U = kChunk / 32;
+    unsigned l = lane_id();
+    bool want[2 * U];
+    uint64_t byte[2 * U];
+    int64_t val[2 * U];
+    bool anyf = false;
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      uint32_t v = c0 + 32 * k + l;
+      bool f = v < n && ld_rlx32((const uint32_t *)&level[v]) == (uint32_t)L;
+      want[2 * k] = want[2 * k + 1] = f;
+      byte[2 * k] = (uint64_t)v * 8;
+      byte[2 * k + 1] = (uint64_t)v * 8 + 8;
+      val[2 * k] = val[2 * k + 1] = 0;
+      anyf |= f;
+    }
+    if (!__any_sync(kFull, anyf)) return true;
+    if (!gather_n<int64_t, 2 * U>(d, a, off_page0, want, byte, val, pc)) return false;
+    // the pages of the lane's short lists (a list of fewer than kHub entries spans at
+    // most two pages); hubs are left to the slice queue, which requests its own
+    uint32_t cnt = 0;
+    uint64_t pg = 0;
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      int64_t s0 = val[2 * k], e0 = val[2 * k + 1];
+      if (!want[2 * k] || e0 <= s0 || e0 - s0 >= kHub) continue;
+      uint64_t p0 = ((uint64_t)s0 * 4) / kPage, p1 = ((uint64_t)(e0 - 1) * 4) / kPage;
+      for (uint64_t p = p0; p <= p1; ++p) {
+        if (cnt == 0 || p != pg) ++cnt;
+        pg = p;
+      }
+    }
+    if (!__all_sync(kFull, cnt <= 1)) return true;  // not sparse: pages when needed
+    bool has = cnt == 1 && !(pc.valid && pc.page == col_page0 + pg);
+    if (!__any_sync(kFull, has)) return true;
+    return warp_request_call(d, has, col_page0 + pg, a.q0, false, a.deadline);
   }
 
   // one 32-vertex unit: every page when needed
@@ -705,6 +766,7 @@ struct BfsAppT {
         if (l == 0) c = atomicAdd(&d.run->work[L & 1], 1u);
         c = __shfl_sync(kFull, c, 0);
         if (c >= nchunks || aborted(d)) break;
+        if (!kDirect && mode == AGILE_ASYNC) ok = prefetch_chunk(d, a, c * kChunk, L, pc);
         for (uint32_t sub = 0; sub < kChunk && ok; sub += 32) ok = chunk(d, a, c * kChunk + sub, L, found, scanned, pc);
         if (!ok) break;
       }

@@ -728,6 +728,15 @@ int agile_set_device_model(agile_ctx *c, uint32_t ndev, uint32_t lat_ns, double 
   }
   AGILE_CUDA_TRY(cudaMemset(c->dev.dev_busy, 0, (size_t)ndev * 8));
   AGILE_CUDA_TRY(cudaMemset(c->dev.emu_busy, 0, (size_t)c->dev.Q * 8));
+  // The device without a model advances only its fetch counters; with a model it also
+  // counts the commands it has seen (arrival stamps).  Between calls every command has
+  // been served, so each queue's "seen" counter is set to its fetch counter.
+  {
+    std::vector<uint32_t> emu((size_t)c->dev.Q * 4);
+    AGILE_CUDA_TRY(cudaMemcpy(emu.data(), c->dev.emu, emu.size() * 4, cudaMemcpyDeviceToHost));
+    for (uint64_t q = 0; q < c->dev.Q; ++q) emu[q * 4 + 1] = emu[q * 4];
+    AGILE_CUDA_TRY(cudaMemcpy(c->dev.emu, emu.data(), emu.size() * 4, cudaMemcpyHostToDevice));
+  }
   c->cfg.num_devices = std::max(c->cfg.num_devices, ndev);
   c->dev.ndev = ndev;
   c->dev.lat_ns = lat_ns;

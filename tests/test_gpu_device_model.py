@@ -163,3 +163,27 @@ def test_writebacks_across_devices_exact_and_once(mode):
         assert np.array_equal(writes, dirtied) and writes.sum() > 0
         assert c.stats()["evictions"] > 0
         assert_cache_invariants(c)
+
+
+def test_model_switch_between_calls():
+    # one context: no model, then an SSD-like model (latency 200 us, 2 devices capped at
+    # 3 GB/s), then no model again; every read is right and the latency holds in between
+    npages = 1200
+    store = _store(npages, 62)
+    with Ctx(store.nbytes, cache_bytes=2048 * 4096, ways=8, num_queues=16, queue_depth=64,
+             trace_records=4096) as c:
+        c.put(0, store)
+        parts = np.array_split(np.arange(npages, dtype=np.uint64), 3)
+        got = _read(c, parts[0])
+        assert np.array_equal(got.reshape(-1), store[:parts[0].size * 4096])
+        ag.agile_set_device_model(c.h, num_devices=2, emu_latency_ns=200_000, emu_device_read_gbps=3.0)
+        ag.agile_reset_stats(c.h)
+        got = _read(c, parts[1])
+        assert np.array_equal(got.reshape(-1), store[parts[1][0] * 4096:(parts[1][-1] + 1) * 4096])
+        tr, n = ag.agile_trace(c.h, 4096)
+        assert n == parts[1].size
+        assert ((tr["t_start"].astype(np.int64) - tr["t_seen"].astype(np.int64)) >= 200_000).all()
+        assert ((tr["q"] % 2) == (tr["page"] % np.uint64(2))).all()
+        ag.agile_set_device_model(c.h)
+        got = _read(c, parts[2])
+        assert np.array_equal(got.reshape(-1), store[parts[2][0] * 4096:])
