@@ -118,8 +118,17 @@ typedef struct {
   uint32_t emu_extra_engines; /* application warps a call leaves idle that also serve the
                                emulated device, at most: 0 = one per CTA of the launch,
                                AGILE_NO_EXTRA_ENGINES = none (only warp 0 of each CTA) */
+  uint32_t prefetch_queues; /* queue pairs that carry requests made ahead of need (the
+                               asynchronous lookahead of the drivers, agile_prefetch);
+                               the device serves the other, demand queues first (NVMe
+                               arbitration with an urgent class), so prefetches only use
+                               device time that demand leaves idle.  0 = half of the
+                               queues (rounded to a multiple of num_devices; none with
+                               fewer than 2 per device), AGILE_NO_PREFETCH_QUEUES = none:
+                               every request shares every queue                      */
 } agile_config;
 #define AGILE_NO_EXTRA_ENGINES 0xFFFFFFFFu
+#define AGILE_NO_PREFETCH_QUEUES 0xFFFFFFFFu
 
 /* Replacement policies of the cache (Sec. 3.4 leaves the policy to the user; Sec. 4.4
  * uses clock).  Both pick a victim within the page's set starting at the set's hand and

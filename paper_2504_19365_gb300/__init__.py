@@ -33,6 +33,7 @@ AGILE_TOKEN_HIT = (1 << 64) - 1
 AGILE_POLICY_CLOCK = 0
 AGILE_POLICY_FIFO = 1
 AGILE_NO_EXTRA_ENGINES = 0xFFFFFFFF
+AGILE_NO_PREFETCH_QUEUES = 0xFFFFFFFF
 
 EXPORTED = [
     "agile_config_default", "agile_init", "agile_destroy", "agile_store_write",
@@ -74,6 +75,7 @@ class agile_config(C.Structure):
         ("emu_device_write_gbps", C.c_double),
         ("share_slots", C.c_uint32),
         ("emu_extra_engines", C.c_uint32),
+        ("prefetch_queues", C.c_uint32),
     ]
 
 

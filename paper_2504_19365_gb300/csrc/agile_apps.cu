@@ -66,7 +66,8 @@ struct EmbApp {
           want = false;
         }
         bool all_hit = false;
-        if (!warp_request(d, want, row_page(r), a.q0, false, a.deadline, nullptr, nullptr, &all_hit)) return false;
+        if (!warp_request(d, want, row_page(r), a.q0, false, a.deadline, nullptr, nullptr, &all_hit, true))
+          return false;
         bo.result(all_hit);
       }
       c.i += take;
@@ -285,7 +286,7 @@ struct PipeApp {
           want = false;
         }
         bool all_hit = false;
-        if (!warp_request(d, want, row_page(k, r), a.q0, false, a.deadline, nullptr, nullptr, &all_hit))
+        if (!warp_request(d, want, row_page(k, r), a.q0, false, a.deadline, nullptr, nullptr, &all_hit, true))
           return false;
         bo.result(all_hit);
       }
@@ -1063,7 +1064,7 @@ struct SpmvAppT {
     uint32_t vend = min(v0 + 32, n);
     uint64_t pa = off_page0 + ((uint64_t)v0 * 8) / kPage, pb = off_page0 + ((uint64_t)vend * 8) / kPage;
     bool want = (lane_id() == 0) || (lane_id() == 1 && pb != pa);
-    return warp_request_call(d, want, lane_id() == 0 ? pa : pb, a.q0, false, a.deadline);
+    return warp_request_call(d, want, lane_id() == 0 ? pa : pb, a.q0, false, a.deadline, true);
   }
 
   // stage B: read the offsets, queue long rows, request the unit's column and value pages
@@ -1090,8 +1091,8 @@ struct SpmvAppT {
     if (kDirect || hi <= lo) return true;
     uint64_t c0 = ((uint64_t)lo * 4) / kPage, c1 = ((uint64_t)(hi - 1) * 4) / kPage;
     bool want = c0 + lane_id() <= c1;
-    if (!warp_request_call(d, want, col_page0 + c0 + lane_id(), a.q0, false, a.deadline)) return false;
-    return warp_request_call(d, want, val_page0 + c0 + lane_id(), a.q0, false, a.deadline);
+    if (!warp_request_call(d, want, col_page0 + c0 + lane_id(), a.q0, false, a.deadline, true)) return false;
+    return warp_request_call(d, want, val_page0 + c0 + lane_id(), a.q0, false, a.deadline, true);
   }
 
   // take queued slices until every slice is taken (the BFS slice queue, one level)

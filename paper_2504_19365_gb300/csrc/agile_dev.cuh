@@ -108,6 +108,7 @@ struct Dev {
   uint32_t sh_mask;  // buckets - 1 (power of two)
   // queues
   uint32_t Q, depth, dmask, dlog;
+  uint32_t Qp;       // queues [Q - Qp, Q) carry prefetches, served after the demand queues
   uint32_t cq_size;  // CQ entries per queue = 2 * depth
   Sqe *sq;
   Cqe *cq;
@@ -130,7 +131,7 @@ struct Dev {
   uint32_t *trace_n;
   // Share Table of user buffers (Sec. 3.4.1): 4 slots per bucket; key = page + 1,
   // buf = the buffer's address, meta = {state:8 | count:32 | closing:1}, tok = the token
-  // of the read that fills the buffer (0 while the entry is being set up)
+  // of the read that fills the buffer (valid once the entry has left PENDING)
   unsigned long long *ub_key, *ub_buf, *ub_meta, *ub_tok;
   uint32_t ub_mask;  // buckets - 1; ub_key == nullptr: no Share Table
   // backing devices: page p lives on device p mod ndev at block p / ndev; queue q
@@ -337,18 +338,23 @@ __host__ __device__ __forceinline__ uint64_t block_of_page(const Dev &d, uint64_
   return d.ndev > 1 ? page / d.ndev : page;
 }
 
-// SQ selection (Sec. 3.3.1): among the queues of the page's device, start at the one
-// nearest the thread's own queue, on a full queue try the device's next one; false
+// SQ selection (Sec. 3.3.1): among the queues of the page's device in the request's
+// class -- demand queues [0, Q - Qp), prefetch queues [Q - Qp, Q) (NVMe-style
+// arbitration: the device serves demand queues first, so requests made ahead of need
+// only use device time that demand leaves idle) -- start at the one nearest the
+// thread's own queue, on a full queue try the class's next one of the device; false
 // after one pass over them.
 __device__ __forceinline__ bool sq_reserve_dev(const Dev &d, uint32_t q0, uint32_t dv, uint32_t n, uint32_t &q,
-                                               uint32_t &slot, uint32_t &ticket) {
+                                               uint32_t &slot, uint32_t &ticket, bool pf = false) {
   const uint32_t nd = d.ndev > 1 ? d.ndev : 1u;
-  const uint32_t per = d.Q / nd;  // queues of one device
+  const uint32_t base = pf && d.Qp ? d.Q - d.Qp : 0u;
+  const uint32_t cnt = d.Qp ? (pf ? d.Qp : d.Q - d.Qp) : d.Q;
+  const uint32_t per = cnt / nd;  // queues of one device in the class
   uint32_t k0 = (q0 / nd) % per;
   for (uint32_t k = 0; k < per; ++k) {
     uint32_t kk = k0 + k;
     if (kk >= per) kk -= per;
-    uint32_t qq = kk * nd + dv;
+    uint32_t qq = base + kk * nd + dv;
     if (sq_try_reserve(d, qq, n, slot, ticket)) {
       q = qq;
       return true;
@@ -483,8 +489,8 @@ __device__ __forceinline__ void sh_remove(const Dev &d, uint64_t slot) {
   st_rlx64(&d.sh_val[slot], 0ull);
   st_rel64(&d.sh_key[slot], 0ull);
 }
-// Token of the read in flight for `page`, 0 when there is none (or it is not published
-// yet).  The key is read again after the value: an entry removed (and maybe reused)
+// Token of the read in flight for `page`, ~0 when there is none (or it is not
+// published yet).  The key is read again after the value: an entry removed (and maybe reused)
 // meanwhile is not taken; one re-inserted for the same page carries a token of the same
 // page, which is as good.
 __device__ __forceinline__ uint64_t sh_token(const Dev &d, uint64_t page) {
@@ -493,9 +499,9 @@ __device__ __forceinline__ uint64_t sh_token(const Dev &d, uint64_t page) {
   for (int k = 0; k < 4; ++k) {
     if (ld_acq64(&d.sh_key[base + k]) != key) continue;
     uint64_t v = ld_acq64(&d.sh_val[base + k]);
-    if (v && ld_acq64(&d.sh_key[base + k]) == key) return v;
+    if (v && ld_acq64(&d.sh_key[base + k]) == key) return v - 1;
   }
-  return 0;
+  return ~0ull;
 }
 
 // ================================================================ cache (Sec. 3.4)
@@ -575,7 +581,7 @@ struct Issued {
 // `sh_own`; the way is claimed BUSY and returned without a read, the caller writes the
 // line and publishes it.  A MODIFIED victim is still written back first.
 static __device__ int cache_miss(const Dev &d, uint64_t page, uint32_t q0, uint32_t &line, Issued &is,
-                          bool fill = true, int64_t sh_own = -1) {
+                          bool fill = true, int64_t sh_own = -1, bool pf = false) {
   int64_t sh = sh_own;
   if (fill) {
     sh = sh_insert(d, page, SH_FILL);
@@ -644,14 +650,15 @@ static __device__ int cache_miss(const Dev &d, uint64_t page, uint32_t q0, uint3
   const bool split = wb && fill && dv_wb != dv_fill;
   uint32_t q = 0, slot = 0, ticket = 0;
   uint32_t nslots = split ? 1u : (wb ? 1u : 0u) + (fill ? 1u : 0u);
-  if (nslots && !sq_reserve_dev(d, q0, wb ? dv_wb : dv_fill, nslots, q, slot, ticket)) {
+  // a write-back rides in the demand class (a fill waits behind it)
+  if (nslots && !sq_reserve_dev(d, q0, wb ? dv_wb : dv_fill, nslots, q, slot, ticket, pf && !wb)) {
     cache_unclaim(d, line, old);
     if (wb) sh_remove(d, (uint64_t)sh_wb);
     if (fill) sh_remove(d, (uint64_t)sh);
     return M_RETRY;
   }
   uint32_t fq = q, fslot = slot, fticket = ticket;  // the read's slot
-  if (split && !sq_reserve_dev(d, q0, dv_fill, 1, fq, fslot, fticket)) {
+  if (split && !sq_reserve_dev(d, q0, dv_fill, 1, fq, fslot, fticket, pf)) {
     sq_commit(d, q, slot, ticket, OP_FLUSH, 0, 0, ctx_make(CTX_NOP, 0, 0));
     cache_unclaim(d, line, old);
     sh_remove(d, (uint64_t)sh_wb);
@@ -694,8 +701,9 @@ static __device__ int cache_miss(const Dev &d, uint64_t page, uint32_t q0, uint3
   }
   sq_commit(d, q, slot, ticket, OP_READ, (uint64_t)line_ptr(d, line), page,
             ctx_make(CTX_FILL, (uint32_t)sh, line));
-  // the read's token, for threads that find the page in flight (Sec. 3.4 case (c))
-  st_rel64(&d.sh_val[sh], ((uint64_t)q << 48) | ((uint64_t)slot << 32) | ticket);
+  // the read's token + 1 (0 = none yet), for threads that find the page in flight
+  // (Sec. 3.4 case (c))
+  st_rel64(&d.sh_val[sh], (((uint64_t)q << 48) | ((uint64_t)slot << 32) | ticket) + 1);
   atomicAdd(stat_ptr(d, S_MISSES), 1ull);
   is.q = q;
   is.slot = slot;
@@ -728,9 +736,10 @@ __device__ __forceinline__ uint64_t make_token(uint32_t q, uint32_t slot, uint32
 // lane itself issued, AGILE_TOKEN_HIT otherwise.
 // `all_hit` (optional) receives, in every lane, whether every leader's page was
 // READY at its first probe (the request had nothing to do).
+// `pf`: the pages are requested ahead of need (prefetch queues, served after demand).
 static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint32_t q0, bool wait,
                              uint64_t deadline, uint64_t *tok = nullptr, int *code = nullptr,
-                             bool *all_hit = nullptr) {
+                             bool *all_hit = nullptr, bool pf = false) {
   unsigned grp = __match_any_sync(kFull, want ? page : ~0ull);
   int lead_lane = __ffs(grp) - 1;
   bool leader = want && lead_lane == (int)lane_id();
@@ -758,7 +767,7 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
         if (first) atomicAdd(stat_ptr(d, S_BUSY_HITS), 1ull);
         if (!wait) need = false;
       } else {
-        int m = cache_miss(d, page, q0, line, is);
+        int m = cache_miss(d, page, q0, line, is, true, -1, pf);
         ring = m == M_ISSUED || m == M_RETRY_RING;
         if (m == M_ISSUED) {
           issued = true;
@@ -835,8 +844,8 @@ __device__ __forceinline__ int warp_probe_pin(const Dev &d, uint64_t page, uint3
 // loops small (fewer spills, fewer instruction-cache misses); a call costs little next
 // to the round trips of a request
 static __device__ __noinline__ bool warp_request_call(const Dev &d, bool want, uint64_t page, uint32_t q0,
-                                                      bool wait, uint64_t deadline) {
-  return warp_request(d, want, page, q0, wait, deadline);
+                                                      bool wait, uint64_t deadline, bool pf = false) {
+  return warp_request(d, want, page, q0, wait, deadline, nullptr, nullptr, nullptr, pf);
 }
 
 template <bool kCall = false>
@@ -938,7 +947,7 @@ static __device__ uint64_t api_issue_read(const Dev &d, const AppCtx &a, bool wa
         need = false;
       } else if (pr == P_BUSY) {
         uint64_t t = sh_token(d, page);
-        if (t) {
+        if (t != ~0ull) {
           tok = t;
           need = false;
         }
@@ -992,7 +1001,7 @@ static __device__ bool api_copy_page(const Dev &d, const AppCtx &a, uint64_t pag
 
 // prefetch (Listing 1 Method-1): start filling the pages of the lanes with `want`.
 static __device__ bool api_prefetch(const Dev &d, const AppCtx &a, bool want, uint64_t page) {
-  return warp_request_call(d, want, page, a.q0, false, a.deadline);
+  return warp_request_call(d, want, page, a.q0, false, a.deadline, true);
 }
 
 // Add rows [j0, j0 + k) (lane j holds row j's line `line_j` and byte offset `off`) to acc
@@ -1395,7 +1404,6 @@ static __device__ void service_loop(const Dev &d, uint32_t n_app, uint64_t deadl
                                     uint32_t nsw) {
   unsigned l = lane_id();
   uint32_t ns = 32;
-  uint32_t windows = (d.Q + 31) / 32;
   for (uint32_t iter = 0;; ++iter) {
     bool progress = false;
     // device engine: serve one queue per iteration, the first one with work found from
@@ -1403,28 +1411,35 @@ static __device__ void service_loop(const Dev &d, uint32_t n_app, uint64_t deadl
     // queue is visited often and commands do not wait behind long scans
     // (the doorbells and fetch counters of four windows of 32 queues are read in one
     // round trip; they only select a queue, emu_serve checks them again)
-    uint32_t r = (uint32_t)(((uint64_t)iter * nsw + sw) % d.Q);
-    uint32_t qsel = ~0u;
-    for (uint32_t w0 = 0; w0 < windows && qsel == ~0u; w0 += 4) {
-      uint32_t dbv[4], fv[4];
+    // (demand queues first: the prefetch queues are served only when no demand queue
+    // has a command the device may take now)
+    for (uint32_t cls = 0; cls < 2 && !progress; ++cls) {
+      uint32_t qsel = ~0u;
+      const uint32_t base = cls ? d.Q - d.Qp : 0u, cnt = cls ? d.Qp : d.Q - d.Qp;
+      if (cnt == 0) continue;
+      const uint32_t r = (uint32_t)(((uint64_t)iter * nsw + sw) % cnt);
+      const uint32_t windows = (cnt + 31) / 32;
+      for (uint32_t w0 = 0; w0 < windows && qsel == ~0u; w0 += 4) {
+        uint32_t dbv[4], fv[4];
 #pragma unroll
-      for (uint32_t j = 0; j < 4; ++j) {
-        uint32_t off = (w0 + j) * 32 + l;
-        dbv[j] = fv[j] = 0;
-        if (off < d.Q) {
-          uint32_t q = (r + off) % d.Q;
-          dbv[j] = ld_rlx32(&d.sq_db[q]);
-          fv[j] = ld_rlx32(&d.emu[q * 4]);
+        for (uint32_t j = 0; j < 4; ++j) {
+          uint32_t off = (w0 + j) * 32 + l;
+          dbv[j] = fv[j] = 0;
+          if (off < cnt) {
+            uint32_t q = base + (r + off) % cnt;
+            dbv[j] = ld_rlx32(&d.sq_db[q]);
+            fv[j] = ld_rlx32(&d.emu[q * 4]);
+          }
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < 4; ++j) {
+          uint32_t off = (w0 + j) * 32 + l;
+          unsigned m = __ballot_sync(kFull, off < cnt && ((dbv[j] - (fv[j] & d.dmask)) & d.dmask) != 0);
+          if (m && qsel == ~0u) qsel = base + (r + (w0 + j) * 32 + (uint32_t)(__ffs(m) - 1)) % cnt;
         }
       }
-#pragma unroll
-      for (uint32_t j = 0; j < 4; ++j) {
-        uint32_t off = (w0 + j) * 32 + l;
-        unsigned m = __ballot_sync(kFull, off < d.Q && ((dbv[j] - (fv[j] & d.dmask)) & d.dmask) != 0);
-        if (m && qsel == ~0u) qsel = (r + (w0 + j) * 32 + (uint32_t)(__ffs(m) - 1)) % d.Q;
-      }
+      if (qsel != ~0u && emu_serve(d, qsel)) progress = true;
     }
-    if (qsel != ~0u && emu_serve(d, qsel)) progress = true;
     // completion side (Alg. 1) for the queues this warp polls
     if (poll)
       for (uint32_t q = sw; q < d.Q; q += nsw) progress |= cq_poll(d, q);

@@ -47,7 +47,7 @@ struct ReadApp {
       if (aborted(d)) return;
       if (prefetch_only) {
         stat_warp(d, S_PREFETCHES, want ? 1u : 0u);
-        if (!warp_request(d, want, page, a.q0, false, a.deadline)) return;
+        if (!warp_request(d, want, page, a.q0, false, a.deadline, nullptr, nullptr, nullptr, true)) return;
         continue;
       }
       uint64_t t = AGILE_TOKEN_HIT;
@@ -391,6 +391,18 @@ __global__ void invalidate_range_kernel(Dev d, uint64_t p0, uint64_t p1) {
 
 // ============================================================================ host API
 
+// Queues that carry prefetches: `req` (0 = half, rounded down to a multiple of the
+// devices; AGILE_NO_PREFETCH_QUEUES = none); -1 when `req` cannot be used.
+static int64_t prefetch_queue_count(uint32_t req, uint32_t Q, uint32_t ndev) {
+  if (req == AGILE_NO_PREFETCH_QUEUES) return 0;
+  if (req == 0) {
+    uint32_t per = Q / ndev;  // queues per device
+    return per >= 2 ? (int64_t)(per / 2) * ndev : 0;
+  }
+  if (req % ndev || req >= Q) return -1;
+  return req;
+}
+
 static void *dalloc(agile_ctx *c, size_t bytes) {
   void *p = nullptr;
   if (bytes == 0) bytes = 16;
@@ -448,6 +460,7 @@ int agile_init(const agile_config *cfg_in, agile_ctx **out) {
   if (cfg.num_devices == 0) cfg.num_devices = 1;
   if (cfg.num_devices > cfg.num_queues || cfg.num_queues % cfg.num_devices) return AGILE_EINVAL;
   if (cfg.cache_policy > AGILE_POLICY_FIFO) return AGILE_EINVAL;
+  if (prefetch_queue_count(cfg.prefetch_queues, cfg.num_queues, cfg.num_devices) < 0) return AGILE_EINVAL;
   if (cfg.wait_timeout_ns == 0) cfg.wait_timeout_ns = 10ull * 1000 * 1000 * 1000;
   if (cfg.prefetch_depth == 0) cfg.prefetch_depth = 1;
 
@@ -487,6 +500,7 @@ int agile_init(const agile_config *cfg_in, agile_ctx **out) {
   while ((uint64_t)buckets < Q * D) buckets <<= 1;
   d.sh_mask = buckets - 1;
   d.Q = (uint32_t)Q;
+  d.Qp = (uint32_t)prefetch_queue_count(cfg.prefetch_queues, cfg.num_queues, cfg.num_devices);
   d.depth = dep;
   d.dmask = dep - 1;
   d.dlog = 0;
@@ -717,6 +731,8 @@ int agile_set_device_model(agile_ctx *c, uint32_t ndev, uint32_t lat_ns, double 
   if (ndev == 0) ndev = 1;
   if (ndev > c->cfg.num_queues || c->cfg.num_queues % ndev) return AGILE_EINVAL;
   if (queue_gbps < 0 || rd_gbps < 0 || wr_gbps < 0) return AGILE_EINVAL;
+  int64_t qp = prefetch_queue_count(c->cfg.prefetch_queues, c->cfg.num_queues, ndev);
+  if (qp < 0) return AGILE_EINVAL;
   AGILE_CUDA_TRY(cudaSetDevice(c->device));
   AGILE_CUDA_TRY(cudaDeviceSynchronize());
   if (ndev > c->cfg.num_devices) {
@@ -739,6 +755,7 @@ int agile_set_device_model(agile_ctx *c, uint32_t ndev, uint32_t lat_ns, double 
   }
   c->cfg.num_devices = std::max(c->cfg.num_devices, ndev);
   c->dev.ndev = ndev;
+  c->dev.Qp = (uint32_t)qp;
   c->dev.lat_ns = lat_ns;
   c->dev.ns_per_page = queue_gbps > 0 ? (uint64_t)llround(kPage / queue_gbps) : 0;
   c->dev.ns_rd_dev = rd_gbps > 0 ? (uint64_t)llround(kPage / rd_gbps) : 0;

@@ -219,8 +219,12 @@ static __device__ int share_acquire(const Dev &d, const AppCtx &a, bool want, ui
         moved = true;
       }
     } else if (phase == 2) {
-      tok = ld_acq64(&d.ub_tok[k]);
-      if (tok) phase = 3;
+      // the fill's token is published before the entry leaves PENDING (any token value,
+      // 0 included, is a valid token)
+      if (ub_state(ld_acq64(&d.ub_meta[k])) != UB_PENDING) {
+        tok = ld_rlx64(&d.ub_tok[k]);
+        phase = 3;
+      }
     }
     warp_ring_is(d, ring, is, a.deadline);
     if (phase < 3 && !moved && gtimer() > a.deadline) {

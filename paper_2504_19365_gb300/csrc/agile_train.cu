@@ -90,7 +90,7 @@ struct BackwardApp {
     uint64_t j = base + lane_id();
     bool head = j < n && (j == 0 || row_at(j) != row_at(j - 1));
     uint64_t pg = head ? page0 + ((uint64_t)row_at(j) * dim * 4) / kPage : 0;
-    return warp_request(d, head, pg, a.q0, false, a.deadline);
+    return warp_request(d, head, pg, a.q0, false, a.deadline, nullptr, nullptr, nullptr, true);
   }
 
   __device__ void run(const Dev &d, const AppCtx &a) const {

@@ -67,7 +67,7 @@ def test_queue_throughput_cap():
     store = _store(npages, 53)
     pages = np.arange(npages, dtype=np.uint64)
     with Ctx(store.nbytes, cache_bytes=2048 * 4096, ways=8, num_queues=q, queue_depth=256,
-             emu_queue_gbps=cap, trace_records=4096) as c:
+             emu_queue_gbps=cap, trace_records=4096, prefetch_queues=ag.AGILE_NO_PREFETCH_QUEUES) as c:
         c.put(0, store)
         _read(c, pages)
         tr, n = ag.agile_trace(c.h, 4096)
@@ -187,3 +187,32 @@ def test_model_switch_between_calls():
         ag.agile_set_device_model(c.h)
         got = _read(c, parts[2])
         assert np.array_equal(got.reshape(-1), store[parts[2][0] * 4096:])
+
+
+def test_demand_queues_are_served_before_prefetch_queues():
+    # the lookup + compute pipeline in async mode requests rows ahead (prefetch queues)
+    # and waits for the rows it sums (demand queues); with the device saturated (one
+    # device capped at 1 GB/s), demand commands wait less for the device than prefetches
+    nt, rows, dim, nbags, pool = 2, 200_000, 64, 512, 16
+    stride = 200_000 * dim * 4
+    tabs = [np.array(synth.table_normal(70 + k, rows, dim)) for k in range(nt)]
+    idx = synth.indices_uniform(72, nt * nbags * pool, rows).reshape(1, nt, nbags, pool)
+    with Ctx(stride * nt, cache_bytes=4096 * 4096, ways=8, num_queues=16, queue_depth=64,
+             emu_device_read_gbps=1.0, trace_records=65536) as c:
+        for k in range(nt):
+            c.put(k * stride, tabs[k])
+        d_idx = torch.from_numpy(idx).to(DEV)
+        out = torch.empty((1, nbags, nt * dim), dtype=torch.float32, device=DEV)
+        ag.agile_config_parallelism(c.h, 32)
+        ag.agile_embedding_pipeline(c.h, 0, stride, nt, rows, dim, d_idx.data_ptr(), pool, nbags, 1, 8,
+                                    out.data_ptr(), ag.AGILE_ASYNC, c.stream)
+        torch.cuda.synchronize()
+        c.check()
+        assert np.array_equal(out.cpu().numpy().view(np.uint32),
+                              oracle.embedding_pipeline(tabs, idx, pool, 8).view(np.uint32))
+        tr, n = ag.agile_trace(c.h, 65536)
+        assert n == tr.size
+        wait = tr["t_start"].astype(np.int64) - tr["t_seen"].astype(np.int64)
+        pf = tr["q"] >= 8                      # queues 8..15 carry the prefetches
+        assert pf.sum() > 100 and (~pf).sum() > 100
+        assert wait[~pf].mean() < wait[pf].mean(), (wait[~pf].mean(), wait[pf].mean())
