@@ -427,6 +427,13 @@ typedef struct {
  * Synchronises the device. */
 AGILE_API int agile_trace(agile_ctx *ctx, agile_trace_rec *host_out, uint32_t cap, uint32_t *n_out);
 
+/* Application events logged since init or the last agile_reset_stats (only with
+ * cfg.trace_records > 0, up to that many): out[2i] = time (GPU global timer, ns),
+ * out[2i+1] = warp | kind << 32 | arg << 40.  The BFS logs, per application warp and
+ * level (arg): kind 1 its own vertices done, 2 the level's long-list slices done, 3 the
+ * level's barrier passed.  *n_out = events logged.  Synchronises the device. */
+AGILE_API int agile_events(agile_ctx *ctx, uint64_t *out, uint32_t cap, uint32_t *n_out);
+
 /* Host-link read bandwidth as the emulated device's engines see it: a kernel of
  * `ctas` CTAs (0 = two per SM) streams `bytes` (a multiple of 4096) from the context's
  * pinned store into d_dst with 16-byte loads, `reps` times; *gbps_out = best rate.

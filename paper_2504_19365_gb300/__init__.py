@@ -46,7 +46,7 @@ EXPORTED = [
     "agile_stats", "agile_reset_stats", "agile_check", "agile_launch_shape", "agile_strerror",
     "agile_config_parallelism", "agile_page_io", "agile_trace", "agile_link_probe", "agile_set_device_model",
     "agile_bfs_hbm", "agile_spmv_hbm", "agile_device_view", "agile_run_reset",
-    "agile_share_replay", "agile_lock_order_check", "agile_embedding_bag_hbm",
+    "agile_share_replay", "agile_lock_order_check", "agile_embedding_bag_hbm", "agile_events",
 ]
 
 
@@ -174,6 +174,7 @@ def lib():
             "agile_strerror": (C.c_char_p, [C.c_int]),
             "agile_page_io": (C.c_int, [vp, u64, u64, vp, vp, vp]),
             "agile_device_view": (C.c_int, [vp, vp, u64]),
+            "agile_events": (C.c_int, [vp, vp, u32, C.POINTER(u32)]),
             "agile_share_replay": (C.c_int, [vp, vp, u32, vp, vp, vp]),
             "agile_lock_order_check": (C.c_int, [vp, u64, vp, u32, C.POINTER(u32)]),
             "agile_run_reset": (C.c_int, [vp, vp]),
@@ -444,6 +445,18 @@ def agile_trace(ctx, cap: int):
     n = C.c_uint32()
     _ok(lib().agile_trace(ctx, out.ctypes.data, cap, C.byref(n)), "agile_trace")
     return out[:min(cap, n.value)], n.value
+
+
+def agile_events(ctx, cap: int):
+    """(times ns, warps, kinds, args) of the application event log, and the number logged."""
+    import numpy as np
+    out = np.zeros(2 * cap, dtype=np.uint64)
+    n = C.c_uint32()
+    _ok(lib().agile_events(ctx, out.ctypes.data, cap, C.byref(n)), "agile_events")
+    k = min(cap, n.value)
+    t, w = out[0:2 * k:2], out[1:2 * k:2]
+    return (t, (w & np.uint64(0xFFFFFFFF)).astype(np.int64), ((w >> np.uint64(32)) & np.uint64(0xFF)).astype(np.int64),
+            (w >> np.uint64(40)).astype(np.int64)), n.value
 
 
 def agile_link_probe(ctx, d_dst, nbytes, ctas=0, reps=3) -> float:

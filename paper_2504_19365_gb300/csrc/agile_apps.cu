@@ -29,6 +29,12 @@ struct EmbApp {
   uint32_t mode;
   uint32_t ahead;  // rows requested ahead of the one being summed (ASYNC), 1..32
   uint32_t group;  // rows pinned together at most (cache-sized), 1..32
+  // bags left by the resident pass: positions 0 .. *list_n - 1 name bags list[pos]
+  // (nullptr: every bag, position = bag); n_bags bounds the positions
+  const uint32_t *list = nullptr;
+  const uint32_t *list_n = nullptr;
+
+  __device__ __forceinline__ uint32_t bag(uint32_t pos) const { return list ? list[pos] : pos; }
 
   __device__ __forceinline__ uint64_t row_page(uint64_t r) const { return page0 + (r * dim * 4) / kPage; }
 
@@ -39,16 +45,16 @@ struct EmbApp {
   };
   __device__ __forceinline__ void cur_init(const AppCtx &a, Cursor &c) const {
     c.b = a.warp;
-    c.i = c.b < n_bags ? off[c.b] : 0;
-    c.e = c.b < n_bags ? off[c.b + 1] : 0;
+    c.i = c.b < n_bags ? off[bag(c.b)] : 0;
+    c.e = c.b < n_bags ? off[bag(c.b) + 1] : 0;
     skip_empty(a, c);
   }
   __device__ __forceinline__ void skip_empty(const AppCtx &a, Cursor &c) const {
     while (c.b < n_bags && c.i >= c.e) {
       c.b += a.n_warps;
       if (c.b < n_bags) {
-        c.i = off[c.b];
-        c.e = off[c.b + 1];
+        c.i = off[bag(c.b)];
+        c.e = off[bag(c.b) + 1];
       }
     }
   }
@@ -93,7 +99,7 @@ struct EmbApp {
     p.cnt = 0;
     p.fast = p.ok = p.leader = false;
     if (b >= n_bags) return;
-    int64_t s = off[b], e = off[b + 1];
+    int64_t s = off[bag(b)], e = off[bag(b) + 1];
     p.cnt = (uint32_t)(e - s);
     p.fast = e > s && e - s <= (int64_t)min(group, 32u);
     if (!p.fast) return;
@@ -127,7 +133,7 @@ struct EmbApp {
 
   __device__ void store_out(uint32_t b, const float4 (&acc)[MF4], uint32_t nf4) const {
     unsigned l = lane_id();
-    float4 *o = (float4 *)(out + (uint64_t)b * dim);
+    float4 *o = (float4 *)(out + (uint64_t)bag(b) * dim);
 #pragma unroll
     for (int k = 0; k < MF4; ++k) {
       uint32_t c = l + 32 * k;
@@ -139,7 +145,7 @@ struct EmbApp {
   __device__ bool slow_bag(const Dev &d, const AppCtx &a, uint32_t b, uint32_t nf4, Cursor &pf, Backoff &bo) const {
     unsigned l = lane_id();
     const bool async = mode == AGILE_ASYNC;
-    int64_t s = off[b], e = off[b + 1];
+    int64_t s = off[bag(b)], e = off[bag(b) + 1];
     float4 acc[MF4];
 #pragma unroll
     for (int k = 0; k < MF4; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -167,6 +173,17 @@ struct EmbApp {
   }
 
   __device__ void run(const Dev &d, const AppCtx &a) const {
+    if (list) {  // only the bags the resident pass left
+      EmbApp me = *this;
+      me.n_bags = min(n_bags, ld_acq32(list_n));
+      me.list_n = nullptr;
+      if (a.warp < me.n_bags) me.run_bags(d, a);
+      return;
+    }
+    run_bags(d, a);
+  }
+
+  __device__ void run_bags(const Dev &d, const AppCtx &a) const {
     unsigned l = lane_id();
     const uint32_t nf4 = dim / 4;
     const bool async = mode == AGILE_ASYNC;
@@ -383,6 +400,9 @@ struct HubEntry {
   unsigned long long pad[3];
 };
 static_assert(sizeof(HubEntry) == 64, "one slice record per 64 bytes");
+
+// events of the BFS in the application event log (agile_events)
+constexpr uint32_t kEvOwnDone = 1, kEvHubsDone = 2, kEvLevelDone = 3;
 
 // A record is published with the number of the launch that wrote it (RunState::epoch,
 // drawn on the device for every launch) and the level, so a record left by an earlier
@@ -625,39 +645,26 @@ struct BfsAppT {
   // request (sparse levels): in dense ones the pages would outnumber what the cache
   // holds for the running warps.
   __device__ bool prefetch_chunk(const Dev &d, const AppCtx &a, uint32_t c0, int32_t L, Pin &pc) const {
-    constexpr int U = kChunk / 32;
+    constexpr uint32_t U = kChunk / 32;
     unsigned l = lane_id();
-    bool want[2 * U];
-    uint64_t byte[2 * U];
-    int64_t val[2 * U];
-    bool anyf = false;
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      uint32_t v = c0 + 32 * k + l;
-      bool f = v < n && ld_rlx32((const uint32_t *)&level[v]) == (uint32_t)L;
-      want[2 * k] = want[2 * k + 1] = f;
-      byte[2 * k] = (uint64_t)v * 8;
-      byte[2 * k + 1] = (uint64_t)v * 8 + 8;
-      val[2 * k] = val[2 * k + 1] = 0;
-      anyf |= f;
-    }
-    if (!__any_sync(kFull, anyf)) return true;
-    if (!gather_n<int64_t, 2 * U>(d, a, off_page0, want, byte, val, pc)) return false;
-    // the pages of the lane's short lists (a list of fewer than kHub entries spans at
-    // most two pages); hubs are left to the slice queue, which requests its own
+    // the lane's page to request (at most one over the chunk's units; two or more
+    // anywhere in the warp: the chunk is not sparse, pages are requested when needed)
     uint32_t cnt = 0;
     uint64_t pg = 0;
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      int64_t s0 = val[2 * k], e0 = val[2 * k + 1];
-      if (!want[2 * k] || e0 <= s0 || e0 - s0 >= kHub) continue;
-      uint64_t p0 = ((uint64_t)s0 * 4) / kPage, p1 = ((uint64_t)(e0 - 1) * 4) / kPage;
-      for (uint64_t p = p0; p <= p1; ++p) {
-        if (cnt == 0 || p != pg) ++cnt;
-        pg = p;
+    for (uint32_t k = 0; k < U; ++k) {
+      uint32_t v = c0 + 32 * k + l;
+      bool f = v < n && ld_rlx32((const uint32_t *)&level[v]) == (uint32_t)L;
+      if (!__any_sync(kFull, f)) continue;
+      int64_t s0 = 0, e0 = 0;
+      if (!read_offsets(d, a, v, f, s0, e0, pc)) return false;
+      if (f && e0 > s0 && e0 - s0 < (int64_t)kHub) {
+        uint64_t p0 = ((uint64_t)s0 * 4) / kPage, p1 = ((uint64_t)(e0 - 1) * 4) / kPage;
+        cnt += (cnt == 0 || p0 != pg) ? 1u : 0u;
+        cnt += p1 != p0 ? 1u : 0u;
+        pg = p1;
       }
+      if (!__all_sync(kFull, cnt <= 1)) return true;  // not sparse: pages when needed
     }
-    if (!__all_sync(kFull, cnt <= 1)) return true;  // not sparse: pages when needed
     bool has = cnt == 1 && !(pc.valid && pc.page == col_page0 + pg);
     if (!__any_sync(kFull, has)) return true;
     return warp_request_call(d, has, col_page0 + pg, a.q0, false, a.deadline);
@@ -776,12 +783,15 @@ struct BfsAppT {
       if (l == 0) {
         fence_ar();
         atomicAdd(&d.run->units_done[L & 1], 1u);
+        app_event(d, a.warp, kEvOwnDone, (uint32_t)L);
       }
       if (ok) help_hubs(d, a, L, found, pc);
       release(d, pc);
       uint32_t tot = __reduce_add_sync(kFull, found);
       if (l == 0 && tot) atomicAdd(&d.run->acc[1 + L % 3], (unsigned long long)tot);
+      if (l == 0) app_event(d, a.warp, kEvHubsDone, (uint32_t)L);
       if (!app_barrier(d, a.n_warps, a.deadline)) return;
+      if (l == 0) app_event(d, a.warp, kEvLevelDone, (uint32_t)L);
       if (aborted(d)) return;
       uint64_t disc = ld_acq64(&d.run->acc[1 + L % 3]);
       if (disc == 0) break;
@@ -1266,6 +1276,99 @@ struct SpmvAppT {
 
 using SpmvApp = SpmvAppT<false>;
 
+// ============================================================================ resident pass
+// First pass of agile_embedding_bag: every bag whose pages are all in the cache is summed
+// here, by a light kernel that runs many warps per SM (no service warps, no miss path),
+// and the others are listed for the engine launch that follows.  Within one call nothing
+// can evict a line before the engine issues its first miss (a context is used by one
+// stream at a time), so the tags are read with plain loads and no line is pinned.  A
+// warp per bag; the pages of the bag's rows are probed once per distinct page (the
+// lowest lane of each group, as the engine does), a hit sets the line's reference bit;
+// a bag of more than 32 indices, with an index out of range or with a page that is not
+// READY / MODIFIED is listed.  The sum is the engine's: rows in increasing index order,
+// FP32, no fusion.
+template <int MF4>
+__global__ void __launch_bounds__(256) resident_bag_kernel(Dev d, uint64_t page0, uint32_t rows, uint32_t dim,
+                                                           const int64_t *idx, const int64_t *off, uint32_t n_bags,
+                                                           float *out, uint32_t *list, uint32_t *list_n) {
+  const unsigned l = threadIdx.x & 31;
+  const uint32_t nf4 = dim / 4;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  constexpr int RB = MF4 >= 4 ? 2 : 16 / MF4;  // rows whose loads are in flight together
+  for (uint64_t b = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; b < n_bags; b += nw) {
+    int64_t s = off[b], e = off[b + 1];
+    int64_t cnt = e - s;
+    bool ok = cnt >= 0 && cnt <= 32;
+    bool want = ok && (int64_t)l < cnt;
+    uint64_t r = want ? (uint64_t)idx[s + l] : 0;
+    if (want && r >= rows) ok = false;
+    uint64_t byte = (want ? r : 0) * dim * 4;
+    uint64_t page = page0 + byte / kPage;
+    uint32_t in = (uint32_t)(byte % kPage);
+    unsigned grp = __match_any_sync(kFull, want ? page : ~0ull);
+    int lead = __ffs(grp) - 1;
+    bool leader = want && lead == (int)l;
+    uint32_t line = 0;
+    bool hit = true;
+    if (leader) {
+      hit = false;
+      uint64_t base = (uint64_t)set_of(page, d.sets) * d.ways;
+      for (uint32_t w = 0; w < d.ways; ++w) {
+        uint64_t t = ld_rlx64(&d.tag[base + w]);
+        uint64_t st = tag_state(t);
+        if ((st == ST_READY || st == ST_MODIFIED) && tag_page(t) == page) {
+          line = (uint32_t)(base + w);
+          hit = true;
+          if (!(t & TAG_REF)) atomicOr(&d.tag[line], TAG_REF);
+          break;
+        }
+      }
+    }
+    bool all = __all_sync(kFull, __all_sync(kFull, ok) && hit);
+    if (!all) {
+      if (l == 0) list[atomicAdd(list_n, 1u)] = (uint32_t)b;
+      continue;
+    }
+    stat_warp(d, S_HITS, leader ? 1u : 0u);
+    stat_warp(d, S_WARP_COALESCED, (want && !leader) ? 1u : 0u);
+    uint32_t myline = __shfl_sync(kFull, line, lead & 31);
+    float4 acc[MF4];
+#pragma unroll
+    for (int c = 0; c < MF4; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (uint32_t j0 = 0; j0 < (uint32_t)cnt; j0 += RB) {
+      float4 v[RB][MF4];
+#pragma unroll
+      for (int jj = 0; jj < RB; ++jj) {
+        uint32_t lj = __shfl_sync(kFull, myline, (j0 + jj) & 31);
+        uint32_t oj = __shfl_sync(kFull, in, (j0 + jj) & 31);
+        const uint8_t *rowp = line_ptr(d, lj) + oj;
+#pragma unroll
+        for (int c = 0; c < MF4; ++c) {
+          uint32_t col = l + 32 * c;
+          v[jj][c] = (j0 + jj < (uint32_t)cnt && col < nf4) ? ld_cg_f4(rowp + 16 * col)
+                                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int jj = 0; jj < RB; ++jj) {
+        if (j0 + jj < (uint32_t)cnt) {
+#pragma unroll
+          for (int c = 0; c < MF4; ++c) {
+            acc[c].x = __fadd_rn(acc[c].x, v[jj][c].x);
+            acc[c].y = __fadd_rn(acc[c].y, v[jj][c].y);
+            acc[c].z = __fadd_rn(acc[c].z, v[jj][c].z);
+            acc[c].w = __fadd_rn(acc[c].w, v[jj][c].w);
+          }
+        }
+      }
+    }
+    float4 *o = (float4 *)(out + b * dim);
+#pragma unroll
+    for (int c = 0; c < MF4; ++c)
+      if (l + 32 * c < nf4) o[l + 32 * c] = acc[c];
+  }
+}
+
 // ============================================================================ plain HBM gather
 // The embedding bag over a table held in HBM, without the cache or the queues: the hit
 // path's ceiling and the "kernel time" of its breakdown.  A warp per bag (bags
@@ -1458,7 +1561,37 @@ int agile_embedding_bag(agile_ctx *c, uint64_t table_byte0, uint32_t rows, uint3
   if (((uintptr_t)d_out) & 15) return AGILE_EINVAL;
   // rows must not straddle pages: dim*4 divides the page
   if (kPage % (dim * 4)) return AGILE_EINVAL;
-  // one warp per bag while the rows each warp holds or requests ahead fit in the cache
+  AGILE_CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t st = as_stream(stream);
+  // scratch: the bags the resident pass leaves to the engine, and their count
+  size_t need = ((size_t)n_bags + 64) * 4;
+  if (c->emb_scratch_bytes < need) {
+    if (c->emb_scratch) cudaFree(c->emb_scratch);
+    c->emb_scratch = nullptr;
+    c->emb_scratch_bytes = 0;
+    AGILE_CUDA_TRY(cudaMalloc(&c->emb_scratch, need));
+    c->emb_scratch_bytes = need;
+  }
+  uint32_t *list_n = (uint32_t *)c->emb_scratch;
+  uint32_t *list = list_n + 32;  // the count on a line of its own
+  AGILE_CUDA_TRY(cudaMemsetAsync(list_n, 0, 4, st));
+  // pass 1: bags whose pages are all resident, at full occupancy
+  {
+    auto resident = [&](auto kern) {
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+      uint64_t grid = (uint64_t)std::max(1, per_sm) * (uint64_t)c->sms;
+      grid = std::min<uint64_t>(grid, ((uint64_t)n_bags + 7) / 8);
+      kern<<<(uint32_t)grid, 256, 0, st>>>(c->dev, table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out,
+                                           list, list_n);
+    };
+    if (dim <= 128) resident(resident_bag_kernel<1>);
+    else if (dim <= 256) resident(resident_bag_kernel<2>);
+    else resident(resident_bag_kernel<kMaxF4>);
+    AGILE_CUDA_TRY(cudaGetLastError());
+  }
+  // pass 2: the engine, on the bags left; one warp per bag while the rows each warp holds
+  // or requests ahead fit in the cache
   uint32_t warps = std::min<uint32_t>(n_bags, warps_for_cache(c, 4, 32));
   auto go = [&](auto tag) {
     using App = decltype(tag);
@@ -1467,7 +1600,7 @@ int agile_embedding_bag(agile_ctx *c, uint64_t table_byte0, uint32_t rows, uint3
     uint64_t ahead = mode == AGILE_ASYNC ? c->dev.nlines / (2ull * run) : 0;
     ahead = std::max<uint64_t>(1, std::min<uint64_t>(32, ahead * c->cfg.prefetch_depth));
     App app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, mode, (uint32_t)ahead,
-            pin_group(c, run)};
+            pin_group(c, run), list, list_n};
     return launch_engine(c, app, stream, warps);
   };
   if (dim <= 128) {

@@ -24,6 +24,8 @@ struct agile_ctx {
   uint64_t bfs_vis_words = 0;
   void *train_scratch = nullptr;  // backward scratch: sorted keys, bag of each position
   size_t train_scratch_bytes = 0;
+  void *emb_scratch = nullptr;  // embedding bag: bags the resident pass left, and their count
+  size_t emb_scratch_bytes = 0;
 };
 
 namespace agile {

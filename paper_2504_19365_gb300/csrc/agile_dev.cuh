@@ -129,6 +129,9 @@ struct Dev {
   struct TraceRec *trace;
   uint32_t trace_cap;
   uint32_t *trace_n;
+  // application event log (optional, same capacity): {time, warp | kind << 32 | arg << 40}
+  unsigned long long *ev;
+  uint32_t *ev_n;
   // Share Table of user buffers (Sec. 3.4.1): 4 slots per bucket; key = page + 1,
   // buf = the buffer's address, meta = {state:8 | count:32 | closing:1}, tok = the token
   // of the read that fills the buffer (valid once the entry has left PENDING)
@@ -245,6 +248,17 @@ __device__ __forceinline__ void stat_warp(const Dev &d, int s, uint32_t v) {
   if (!b) return;
   uint32_t sum = __reduce_add_sync(kFull, v);
   if (lane_id() == 0) atomicAdd(stat_ptr(d, s), (unsigned long long)sum);
+}
+
+// Application event (lane 0 of a warp; only with the trace on): `kind` names the
+// event, `arg` a small number (a level, ...).
+__device__ __forceinline__ void app_event(const Dev &d, uint32_t warp, uint32_t kind, uint32_t arg) {
+  if (!d.ev) return;
+  uint32_t i = atomicAdd(d.ev_n, 1u);
+  if (i < d.trace_cap) {
+    d.ev[2 * i] = gtimer();
+    d.ev[2 * i + 1] = (uint64_t)warp | ((uint64_t)(kind & 0xFF) << 32) | ((uint64_t)(arg & 0xFFFFFF) << 40);
+  }
 }
 
 // A cache line of `page` turned from clean to MODIFIED (or a write-through was issued):
@@ -560,15 +574,68 @@ __device__ __forceinline__ void cache_unclaim(const Dev &d, uint32_t line, uint6
   }
 }
 
-// M_RETRY_RING: as M_RETRY, but a no-op command was committed to (q, slot, ticket) and
-// must be rung.
-enum Miss { M_ISSUED = 0, M_HIT = 1, M_BUSY = 2, M_RETRY = 3, M_RETRY_RING = 4 };
+enum Miss { M_ISSUED = 0, M_HIT = 1, M_BUSY = 2, M_RETRY = 3 };
 
 struct Issued {
-  uint32_t q, slot, ticket;     // the command to ring (the read, when there is one)
-  uint32_t q2, slot2, ticket2;  // a second command on another queue (q2 = ~0: none)
+  uint32_t q, slot, ticket;  // the command to ring (the read, when there is one)
   int code;  // 1 fill, 2 evict READY, 3 write-back MODIFIED
 };
+
+// One thread rings queue q until its command (slot, ticket) has left UPDATED (the
+// doorbell-lock holder never needs a cache line, so this wait cannot close a cycle);
+// false after the context's wait bound.
+static __device__ __noinline__ bool lane_ring(const Dev &d, uint32_t q, uint32_t slot, uint32_t ticket) {
+  uint64_t deadline = gtimer() + d.timeout_ns;
+  uint32_t ns = 32;
+  while (!sq_attempt_db(d, q, slot, ticket)) {
+    if (gtimer() > deadline) {
+      set_error(d, -110);
+      return false;
+    }
+    backoff(ns);
+  }
+  return true;
+}
+
+// The rare miss whose MODIFIED victim lives on another device than the page that
+// replaces it: the write-back takes a demand slot of its device, the read a slot of the
+// page's device.  If the read's slot cannot be had, the write-back's slot is spent on a
+// no-op command (a reserved slot must be committed) and the miss is retried holding
+// nothing.  The write-back is rung here; the read is left to the caller in `is`.
+// Out of line, so that the common miss path stays small.
+static __device__ __noinline__ int cache_miss_split(const Dev &d, uint64_t page, uint32_t q0, uint32_t line,
+                                                    Issued &is, uint64_t old, int64_t sh, int64_t sh_wb, bool pf) {
+  uint32_t wq = 0, wslot = 0, wticket = 0, q = 0, slot = 0, ticket = 0;
+  if (!sq_reserve_dev(d, q0, dev_of_page(d, tag_page(old)), 1, wq, wslot, wticket, false)) {
+    cache_unclaim(d, line, old);
+    sh_remove(d, (uint64_t)sh_wb);
+    sh_remove(d, (uint64_t)sh);
+    return M_RETRY;
+  }
+  if (!sq_reserve_dev(d, q0, dev_of_page(d, page), 1, q, slot, ticket, pf)) {
+    sq_commit(d, wq, wslot, wticket, OP_FLUSH, 0, 0, ctx_make(CTX_NOP, 0, 0));
+    cache_unclaim(d, line, old);
+    sh_remove(d, (uint64_t)sh_wb);
+    sh_remove(d, (uint64_t)sh);
+    lane_ring(d, wq, wslot, wticket);
+    return M_RETRY;
+  }
+  atomicAdd(stat_ptr(d, S_EVICTIONS), 1ull);
+  uint8_t *stg = d.staging + ((uint64_t)wq * d.depth + wslot) * kPage;
+  lane_copy_page(stg, line_ptr(d, line));
+  fence_ar();
+  sq_commit(d, wq, wslot, wticket, OP_WRITE, (uint64_t)stg, tag_page(old), ctx_make(CTX_WB, (uint32_t)sh_wb, 0));
+  atomicAdd(stat_ptr(d, S_WRITEBACKS), 1ull);
+  lane_ring(d, wq, wslot, wticket);
+  sq_commit(d, q, slot, ticket, OP_READ, (uint64_t)line_ptr(d, line), page, ctx_make(CTX_FILL, (uint32_t)sh, line));
+  st_rel64(&d.sh_val[sh], (((uint64_t)q << 48) | ((uint64_t)slot << 32) | ticket) + 1);
+  atomicAdd(stat_ptr(d, S_MISSES), 1ull);
+  is.q = q;
+  is.slot = slot;
+  is.ticket = ticket;
+  is.code = 3;
+  return M_ISSUED;
+}
 
 // Cases (b) and (d) for one thread: take ownership of the page's miss in the share
 // table, pick a way (lowest INVALID way, else the clock: a set reference bit is
@@ -640,39 +707,23 @@ static __device__ int cache_miss(const Dev &d, uint64_t page, uint32_t q0, uint3
   }
   line = (uint32_t)(base + victim);
   bool wb = tag_state(old) == ST_MODIFIED;
-  // Queue slots: the write-back and the read go to the queues of their pages' devices.
-  // On one device they take two consecutive slots of one queue, reserved together; on
-  // two devices the write-back's slot is reserved first, and if the read then finds no
-  // slot the write-back slot is spent on a no-op command (a slot once reserved must be
-  // committed) and the miss is retried holding nothing.
-  const uint32_t dv_fill = dev_of_page(d, page);
-  const uint32_t dv_wb = wb ? dev_of_page(d, tag_page(old)) : dv_fill;
-  const bool split = wb && fill && dv_wb != dv_fill;
+  if (wb && fill && d.ndev > 1 && dev_of_page(d, tag_page(old)) != dev_of_page(d, page))
+    return cache_miss_split(d, page, q0, line, is, old, sh, sh_wb, pf);
+  // a write-back and its refill take two consecutive slots of one queue of their
+  // device, reserved together (a write-back rides in the demand class: a fill waits
+  // behind it)
   uint32_t q = 0, slot = 0, ticket = 0;
-  uint32_t nslots = split ? 1u : (wb ? 1u : 0u) + (fill ? 1u : 0u);
-  // a write-back rides in the demand class (a fill waits behind it)
-  if (nslots && !sq_reserve_dev(d, q0, wb ? dv_wb : dv_fill, nslots, q, slot, ticket, pf && !wb)) {
+  uint32_t nslots = (wb ? 1u : 0u) + (fill ? 1u : 0u);
+  if (nslots && !sq_reserve_dev(d, q0, dev_of_page(d, wb ? tag_page(old) : page), nslots, q, slot, ticket,
+                                pf && !wb)) {
     cache_unclaim(d, line, old);
     if (wb) sh_remove(d, (uint64_t)sh_wb);
     if (fill) sh_remove(d, (uint64_t)sh);
     return M_RETRY;
   }
-  uint32_t fq = q, fslot = slot, fticket = ticket;  // the read's slot
-  if (split && !sq_reserve_dev(d, q0, dv_fill, 1, fq, fslot, fticket, pf)) {
-    sq_commit(d, q, slot, ticket, OP_FLUSH, 0, 0, ctx_make(CTX_NOP, 0, 0));
-    cache_unclaim(d, line, old);
-    sh_remove(d, (uint64_t)sh_wb);
-    sh_remove(d, (uint64_t)sh);
-    is.q = q;  // the no-op is rung like any command
-    is.slot = slot;
-    is.ticket = ticket;
-    is.q2 = 0xFFFFFFFFu;
-    return M_RETRY_RING;
-  }
   is.q = q;
   is.slot = slot;
   is.ticket = ticket;
-  is.q2 = 0xFFFFFFFFu;
   is.code = wb ? 3 : (old ? 2 : 1);
   if (old) atomicAdd(stat_ptr(d, S_EVICTIONS), 1ull);
   if (wb) {
@@ -683,17 +734,8 @@ static __device__ int cache_miss(const Dev &d, uint64_t page, uint32_t q0, uint3
               ctx_make(CTX_WB, (uint32_t)sh_wb, 0));
     atomicAdd(stat_ptr(d, S_WRITEBACKS), 1ull);
     if (!fill) return M_ISSUED;  // the write-back is the command to ring
-    if (split) {
-      is.q2 = q;  // ring the write-back's queue too; the read is the request's command
-      is.slot2 = slot;
-      is.ticket2 = ticket;
-      q = fq;
-      slot = fslot;
-      ticket = fticket;
-    } else {
-      slot = (slot + 1) & d.dmask;
-      ticket += 1;
-    }
+    slot = (slot + 1) & d.dmask;
+    ticket += 1;
   }
   if (!fill) {
     is.q = 0xFFFFFFFFu;  // nothing to ring
@@ -705,19 +747,9 @@ static __device__ int cache_miss(const Dev &d, uint64_t page, uint32_t q0, uint3
   // (Sec. 3.4 case (c))
   st_rel64(&d.sh_val[sh], (((uint64_t)q << 48) | ((uint64_t)slot << 32) | ticket) + 1);
   atomicAdd(stat_ptr(d, S_MISSES), 1ull);
-  is.q = q;
   is.slot = slot;
   is.ticket = ticket;
   return M_ISSUED;
-}
-
-// warp_ring for what cache_miss committed: the command (q, slot, ticket) and, when a
-// write-back went to another device's queue, that one too.
-__device__ __forceinline__ bool warp_ring_is(const Dev &d, bool has, const Issued &is, uint64_t deadline) {
-  bool ok = warp_ring(d, has, is.q, is.slot, is.ticket, deadline);
-  bool two = has && is.q2 != 0xFFFFFFFFu;
-  if (__any_sync(kFull, two)) ok = warp_ring(d, two, is.q2, is.slot2, is.ticket2, deadline) && ok;
-  return ok;
 }
 
 __device__ __forceinline__ uint64_t make_token(uint32_t q, uint32_t slot, uint32_t ticket) {
@@ -756,7 +788,6 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
   while (__any_sync(kFull, need)) {
     bool issued = false, ring = false;
     Issued is{};
-    is.q2 = 0xFFFFFFFFu;
     if (need) {
       int pr = cache_probe(d, page, false, line);
       if (first && pr != P_HIT) first_miss = true;
@@ -768,7 +799,7 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
         if (!wait) need = false;
       } else {
         int m = cache_miss(d, page, q0, line, is, true, -1, pf);
-        ring = m == M_ISSUED || m == M_RETRY_RING;
+        ring = m == M_ISSUED;
         if (m == M_ISSUED) {
           issued = true;
           if (tok) *tok = make_token(is.q, is.slot, is.ticket);
@@ -784,7 +815,7 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
       }
     }
     first = false;
-    if (!warp_ring_is(d, ring, is, deadline)) ok = false;
+    if (!warp_ring(d, ring, is.q, is.slot, is.ticket, deadline)) ok = false;
     if (__any_sync(kFull, need)) {
       if (need) {
         if (gtimer() > deadline || aborted(d)) {
@@ -939,7 +970,6 @@ static __device__ uint64_t api_issue_read(const Dev &d, const AppCtx &a, bool wa
   while (__any_sync(kFull, need)) {
     bool ring = false;
     Issued is{};
-    is.q2 = 0xFFFFFFFFu;
     if (need) {
       uint32_t line = 0;
       int pr = cache_probe(d, page, false, line);
@@ -953,7 +983,7 @@ static __device__ uint64_t api_issue_read(const Dev &d, const AppCtx &a, bool wa
         }
       } else {
         int m = cache_miss(d, page, a.q0, line, is);
-        ring = m == M_ISSUED || m == M_RETRY_RING;
+        ring = m == M_ISSUED;
         if (m == M_ISSUED) {
           tok = make_token(is.q, is.slot, is.ticket);
           need = false;
@@ -963,7 +993,7 @@ static __device__ uint64_t api_issue_read(const Dev &d, const AppCtx &a, bool wa
       }
       if (need && (gtimer() > a.deadline || aborted(d))) need = false;
     }
-    warp_ring_is(d, ring, is, a.deadline);
+    warp_ring(d, ring, is.q, is.slot, is.ticket, a.deadline);
     if (__any_sync(kFull, need)) backoff(ns, 1024);
   }
   tok = __shfl_sync(kFull, tok, lead & 31);
@@ -1413,6 +1443,7 @@ static __device__ void service_loop(const Dev &d, uint32_t n_app, uint64_t deadl
     // round trip; they only select a queue, emu_serve checks them again)
     // (demand queues first: the prefetch queues are served only when no demand queue
     // has a command the device may take now)
+#pragma unroll 1
     for (uint32_t cls = 0; cls < 2 && !progress; ++cls) {
       uint32_t qsel = ~0u;
       const uint32_t base = cls ? d.Q - d.Qp : 0u, cnt = cls ? d.Qp : d.Q - d.Qp;

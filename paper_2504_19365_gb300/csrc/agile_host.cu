@@ -118,9 +118,7 @@ struct WriteApp {
       int how = -1;  // 0 pinned hit, 1 claimed
       Issued is{};
       is.q = 0xFFFFFFFFu;
-      is.q2 = 0xFFFFFFFFu;
       for (;;) {
-        bool noop = false;
         if (l == 0) {
           int pr = cache_probe(d, page, true, line);
           if (pr == P_HIT) {
@@ -128,14 +126,12 @@ struct WriteApp {
           } else if (pr == P_MISS) {
             int m = cache_miss(d, page, a.q0, line, is, false, sh);
             how = (m == M_ISSUED) ? 1 : -1;
-            noop = m == M_RETRY_RING;
           } else {
             how = -1;
           }
         }
         how = __shfl_sync(kFull, how, 0);
         if (how >= 0) break;
-        if (!warp_ring_is(d, noop, is, a.deadline)) return;
         if (gtimer() > a.deadline || aborted(d)) {
           if (l == 0) {
             set_error(d, -110);
@@ -146,7 +142,7 @@ struct WriteApp {
         backoff(ns);
       }
       line = __shfl_sync(kFull, line, 0);
-      if (!warp_ring_is(d, l == 0 && is.q != 0xFFFFFFFFu, is, a.deadline)) return;
+      if (!warp_ring(d, l == 0 && is.q != 0xFFFFFFFFu, is.q, is.slot, is.ticket, a.deadline)) return;
       // 3. new contents into the line; publish it READY (a full page supersedes it)
       warp_copy_page(line_ptr(d, line), src + i * kPage);
       __threadfence();
@@ -292,7 +288,6 @@ struct ReplayApp {
         int done = 0, issued = 0, ring = 0;
         uint32_t line = 0;
         Issued is{};
-        is.q2 = 0xFFFFFFFFu;
         if (l == 0) {
           int pr = cache_probe(d, page, false, line);
           if (pr == P_HIT) {
@@ -300,7 +295,7 @@ struct ReplayApp {
             atomicAdd(stat_ptr(d, S_HITS), 1ull);
           } else if (pr == P_MISS) {
             int m = cache_miss(d, page, a.q0, line, is);
-            ring = m == M_ISSUED || m == M_RETRY_RING;
+            ring = m == M_ISSUED;
             if (m == M_ISSUED) {
               issued = 1;
               code = is.code;
@@ -310,7 +305,7 @@ struct ReplayApp {
         done = __shfl_sync(kFull, done, 0);
         if (done) break;
         issued = __shfl_sync(kFull, issued, 0);
-        if (!warp_ring_is(d, l == 0 && ring, is, a.deadline)) return;
+        if (!warp_ring(d, l == 0 && ring, is.q, is.slot, is.ticket, a.deadline)) return;
         if (issued) {
           // wait for the fill with nothing held
           line = __shfl_sync(kFull, line, 0);
@@ -540,6 +535,8 @@ int agile_init(const agile_config *cfg_in, agile_ctx **out) {
   d.trace_cap = cfg.trace_records;
   d.trace = cfg.trace_records ? (TraceRec *)A((uint64_t)cfg.trace_records * sizeof(TraceRec)) : nullptr;
   d.trace_n = (uint32_t *)A(16);
+  d.ev = cfg.trace_records ? (unsigned long long *)A((uint64_t)cfg.trace_records * 16) : nullptr;
+  d.ev_n = (uint32_t *)A(16);
   d.ndev = cfg.num_devices;
   d.policy = cfg.cache_policy;
   d.dev_busy = (unsigned long long *)A((uint64_t)cfg.num_devices * 8);
@@ -604,6 +601,7 @@ int agile_destroy(agile_ctx *c) {
   if (c->bfs_hubq) cudaFree(c->bfs_hubq);
   if (c->bfs_vis) cudaFree(c->bfs_vis);
   if (c->train_scratch) cudaFree(c->train_scratch);
+  if (c->emb_scratch) cudaFree(c->emb_scratch);
   if (c->store_host) cudaFreeHost(c->store_host);
   delete c;
   return AGILE_OK;
@@ -722,6 +720,19 @@ int agile_reset_stats(agile_ctx *c) {
   AGILE_CUDA_TRY(cudaMemset(c->dev.pg_writes, 0, pages * 4));
   AGILE_CUDA_TRY(cudaMemset(c->dev.pg_dirty, 0, pages * 4));
   AGILE_CUDA_TRY(cudaMemset(c->dev.trace_n, 0, 4));
+  AGILE_CUDA_TRY(cudaMemset(c->dev.ev_n, 0, 4));
+  return AGILE_OK;
+}
+
+int agile_events(agile_ctx *c, uint64_t *out, uint32_t cap, uint32_t *n_out) {
+  if (!c || (cap && !out)) return AGILE_EINVAL;
+  AGILE_CUDA_TRY(cudaSetDevice(c->device));
+  AGILE_CUDA_TRY(cudaDeviceSynchronize());
+  uint32_t n = 0;
+  AGILE_CUDA_TRY(cudaMemcpy(&n, c->dev.ev_n, 4, cudaMemcpyDeviceToHost));
+  if (n_out) *n_out = n;
+  uint32_t k = std::min(std::min(n, c->dev.trace_cap), cap);
+  if (k && c->dev.ev) AGILE_CUDA_TRY(cudaMemcpy(out, c->dev.ev, (size_t)k * 16, cudaMemcpyDeviceToHost));
   return AGILE_OK;
 }
 

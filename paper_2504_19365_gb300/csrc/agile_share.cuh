@@ -193,7 +193,6 @@ static __device__ int share_acquire(const Dev &d, const AppCtx &a, bool want, ui
     bool ring = false;
     Issued is{};
     is.q = 0xFFFFFFFFu;
-    is.q2 = 0xFFFFFFFFu;
     bool moved = false;
     if (phase == 0) {
       k = ub_find(d, page);
@@ -226,7 +225,7 @@ static __device__ int share_acquire(const Dev &d, const AppCtx &a, bool want, ui
         phase = 3;
       }
     }
-    warp_ring_is(d, ring, is, a.deadline);
+    warp_ring(d, ring, is.q, is.slot, is.ticket, a.deadline);
     if (phase < 3 && !moved && gtimer() > a.deadline) {
       rc = AGILE_ETIMEDOUT;  // an entry set up by this lane stays PENDING: the launch is failing anyway
       set_error(d, -110);
@@ -271,7 +270,6 @@ static __device__ int share_release(const Dev &d, const AppCtx &a, bool want, ui
     bool ring = false;
     Issued is{};
     is.q = 0xFFFFFFFFu;
-    is.q2 = 0xFFFFFFFFu;
     bool moved = false;
     if (phase == 0) {
       k = ub_find(d, page);
@@ -307,7 +305,7 @@ static __device__ int share_release(const Dev &d, const AppCtx &a, bool want, ui
       st_rel64(&d.ub_key[k], 0ull);
       phase = 2;
     }
-    warp_ring_is(d, ring, is, a.deadline);
+    warp_ring(d, ring, is.q, is.slot, is.ticket, a.deadline);
     if (phase < 2 && !moved && gtimer() > a.deadline) {
       rc = AGILE_ETIMEDOUT;
       set_error(d, -110);
