@@ -316,10 +316,10 @@ AGILE_API int agile_spmv_hbm(agile_ctx *ctx, const int64_t *d_offsets, const int
  * would stall other streams.  The paper has no counterpart: it is an addition of this
  * library.  agile_bfs allocates a queue of long adjacency lists and a visited bitmap on
  * first use; this entry point uses fixed device arrays compiled into the library
- * instead (2 MiB and 4 MiB, held by every GPU that loads the library until the process
+ * instead (8 MiB and 4 MiB, held by every GPU that loads the library until the process
  * exits) and calls no cudaMalloc/cudaFree.  n_cols: number of int32 column entries of
- * the graph; graphs with more than 33,553,408 column entries (32,768 queue slots of
- * 1,024 entries) or more than 33,554,432 vertices are rejected with AGILE_EINVAL and a
+ * the graph; graphs with more than 33,554,176 column entries (131,072 queue slots of
+ * 256 entries) or more than 33,554,432 vertices are rejected with AGILE_EINVAL and a
  * message on stderr.  The first call on a device looks up the arrays' device addresses
  * (make that first call before any stream capture); the addresses are kept for the
  * process, so a device reset (cudaDeviceReset) between calls is not supported.  All

@@ -431,7 +431,11 @@ struct BfsAppT {
   __device__ __forceinline__ uint64_t tag(const Dev &d, int32_t L) const {
     return (launch_epoch(d) << 32) | (uint32_t)(L + 1);
   }
-  static constexpr uint32_t kHub = 1024;
+  // lists of at least kHub entries go to the shared slice queue: a unit's owner scans at
+  // most 32 x (kHub - 1) entries itself, so one warp holding heavy units cannot hold up
+  // a level (the events of a level-2 trace showed the slowest warp at 2.6x the median
+  // with kHub = 1024)
+  static constexpr uint32_t kHub = 256;
   static constexpr uint32_t kSlice = 2048;
 
   struct Pin {
@@ -1485,7 +1489,7 @@ int bfs_launch(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32
 // allocation's implicit device synchronisation would stall every other stream.  For
 // them agile_bfs_noalloc keeps the long-list queue, the only scratch the BFS kernel
 // needs beyond the context, in this fixed device array, and the visited bitmap in a
-// second one.  Every GPU that loads the library holds them (2 MiB + 4 MiB) until the
+// second one.  Every GPU that loads the library holds them (8 MiB + 4 MiB) until the
 // process exits.  Host code must not pass the array's name to a kernel: on the host it
 // is a stand-in symbol, not a device address, so its address is fetched once per device
 // with cudaGetSymbolAddress, with that device current, on the first call on that device
@@ -1496,7 +1500,7 @@ int bfs_launch(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32
 // taken for a live entry; the bitmap is cleared by every call.  All calls on one device
 // share the arrays, so calls of this entry point that overlap on that GPU (from any
 // context or stream) race on them.
-constexpr uint32_t kNoAllocHubMax = 32768;
+constexpr uint32_t kNoAllocHubMax = 131072;  // entries / kHub records: graphs up to 33,554,176 entries
 constexpr uint32_t kNoAllocVisWords = 1u << 20;  // vertices up to 2^25
 static __device__ __align__(256) HubEntry g_bfs_hub_scratch[kNoAllocHubMax];
 static __device__ __align__(256) uint32_t g_bfs_vis_scratch[kNoAllocVisWords];
@@ -1523,10 +1527,11 @@ int noalloc_scratch(int device, HubEntry **out, uint32_t **vis_out) {
   return AGILE_OK;
 }
 
-// Slice queue of a CSR walk (BFS, SpMV).  A list of d >= kHub entries takes
-// ceil(d / kSlice) records: at most d / 1024 for the BFS (kSlice = 2048 = 2 kHub), at
-// most 2 d / 1024 for the SpMV (kSlice = kHub); the entries the store can hold beyond
-// cols_byte0 bound d.  `per_1024`: records per 1024 entries.
+// Slice queue of a CSR walk (BFS, SpMV): at most `per_1024` records per 1024 column
+// entries of a level -- the BFS's slices hold at least kHub = 256 entries (4), the
+// SpMV's ceil(d / 1024) of a row of d >= 1024 entries at most 2 d / 1024 (2); the
+// entries the store can hold beyond cols_byte0 bound them.  A reservation past the
+// queue's end is still correct: the warp scans those lists itself.
 int ensure_slice_entries(agile_ctx *c, uint64_t entries, uint32_t per_1024);
 int ensure_slice_queue(agile_ctx *c, uint64_t cols_byte0, uint32_t per_1024 = 1) {
   return ensure_slice_entries(c, (c->cfg.store_bytes - cols_byte0) / 4, per_1024);
@@ -1649,7 +1654,7 @@ int agile_bfs(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_
   int r = bfs_check(c, offsets_byte0, cols_byte0, n_vertices, src, d_level, mode);
   if (r) return r;
   AGILE_CUDA_TRY(cudaSetDevice(c->device));
-  r = ensure_slice_queue(c, cols_byte0);
+  r = ensure_slice_queue(c, cols_byte0, 1024 / BfsApp::kHub);
   if (r) return r;
   uint64_t words = ((uint64_t)n_vertices + 31) / 32;
   if (!c->bfs_vis || c->bfs_vis_words < words) {
@@ -1725,7 +1730,7 @@ int agile_bfs_hbm(agile_ctx *c, const int64_t *d_offsets, const int32_t *d_cols,
   if (!c || !d_offsets || !d_cols || !d_level) return AGILE_EINVAL;
   if (n_vertices == 0 || src < 0 || (uint32_t)src >= n_vertices) return AGILE_EINVAL;
   AGILE_CUDA_TRY(cudaSetDevice(c->device));
-  int r = ensure_slice_entries(c, n_cols, 1);
+  int r = ensure_slice_entries(c, n_cols, 1024 / BfsApp::kHub);
   if (r) return r;
   uint64_t words = ((uint64_t)n_vertices + 31) / 32;
   if (!c->bfs_vis || c->bfs_vis_words < words) {

@@ -397,7 +397,9 @@ __device__ __forceinline__ void sq_commit(const Dev &d, uint32_t q, uint32_t slo
   st_cg16(e + 8, c);
   st_cg16(e + 12, f);
   st_rlx64(&d.cmd_ctx[i], ctx);
-  fence_ar();
+  // the release orders the command's stores (and the caller's earlier ones) before the
+  // state: whoever acquires UPDATED -- the doorbell-lock holder, then the device through
+  // the doorbell -- sees them
   st_rel64(&d.sqe_state[i], ((uint64_t)ticket << 2) | SQE_UPDATED);
 }
 
@@ -627,8 +629,8 @@ static __device__ __noinline__ int cache_miss_split(const Dev &d, uint64_t page,
   sq_commit(d, wq, wslot, wticket, OP_WRITE, (uint64_t)stg, tag_page(old), ctx_make(CTX_WB, (uint32_t)sh_wb, 0));
   atomicAdd(stat_ptr(d, S_WRITEBACKS), 1ull);
   lane_ring(d, wq, wslot, wticket);
+  st_rlx64(&d.sh_val[sh], (((uint64_t)q << 48) | ((uint64_t)slot << 32) | ticket) + 1);
   sq_commit(d, q, slot, ticket, OP_READ, (uint64_t)line_ptr(d, line), page, ctx_make(CTX_FILL, (uint32_t)sh, line));
-  st_rel64(&d.sh_val[sh], (((uint64_t)q << 48) | ((uint64_t)slot << 32) | ticket) + 1);
   atomicAdd(stat_ptr(d, S_MISSES), 1ull);
   is.q = q;
   is.slot = slot;
@@ -647,6 +649,139 @@ static __device__ __noinline__ int cache_miss_split(const Dev &d, uint64_t page,
 // fill=false (writes of whole pages): the caller already owns the page's share entry
 // `sh_own`; the way is claimed BUSY and returned without a read, the caller writes the
 // line and publishes it.  A MODIFIED victim is still written back first.
+// Victim search of a miss in `set` (Sec. 3.4 cases (b) and (d)): the lowest way with
+// an INVALID, unpinned tag, else the clock sweep from the set's hand (a way whose
+// reference bit is set has it cleared and is passed; BUSY, pinned and written-back
+// ways are passed; under FIFO no bit is looked at).  The chosen way is claimed by
+// compare-and-swap from the tag that was read, as BUSY for the new page (`claimed`).
+// Returns the way (old = its tag before, 0 when it was INVALID; sh_wb = the Share
+// Table entry of the write-back of a MODIFIED victim) or -1.
+//
+// Sets of at most 8 ways are read once (tags and hand) and the sweep runs on that
+// copy: the hand advance and the cleared reference bits are published only once the
+// claim has succeeded (fire-and-forget atomics), and a failed claim reads the set
+// again.  With one request in flight the decisions are those of the stepwise sweep.
+static __device__ __noinline__ int64_t pick_victim(const Dev &d, uint32_t set, uint64_t claimed, uint64_t &old,
+                                                   int64_t &sh_wb) {
+  const uint32_t ways = d.ways;
+  const uint64_t base = (uint64_t)set * ways;
+  const bool clock = d.policy == kPolicyClock;
+  if (ways <= 8) {
+#pragma unroll 1
+    for (int attempt = 0; attempt < 8; ++attempt) {
+      uint64_t t[8];
+      if (ways == 8) {
+        ld_tags8(&d.tag[base], t);
+      } else {
+#pragma unroll
+        for (uint32_t w = 0; w < 8; ++w) t[w] = w < ways ? ld_rlx64(&d.tag[base + w]) : 0ull;
+      }
+      const uint32_t h = ld_rlx32(&d.hand[set]) % ways;
+      // (b) the lowest free way
+#pragma unroll
+      for (uint32_t w = 0; w < 8; ++w)
+        if (w < ways && t[w] == 0 &&
+            atomicCAS(&d.tag[base + w], 0ull, (unsigned long long)claimed) == 0ull) {
+          old = 0;
+          return w;
+        }
+      // (d) the sweep as bit masks over the ways: `take` ways end it when the hand
+      // reaches them (INVALID and unpinned, or evictable with a clear bit); `ref`
+      // ways are passed once with their bit cleared and end the second pass.
+      uint32_t take = 0, ref = 0;
+#pragma unroll
+      for (uint32_t w = 0; w < 8; ++w) {
+        if (w >= ways) continue;
+        uint64_t st = tag_state(t[w]);
+        bool pinned = (t[w] & PIN_MASK) != 0;
+        if (st == ST_INVALID) {
+          if (!pinned) take |= 1u << w;
+        } else if (st != ST_BUSY && !pinned && !(t[w] & TAG_WB)) {
+          if (clock && (t[w] & TAG_REF)) ref |= 1u << w;
+          else take |= 1u << w;
+        }
+      }
+      if (!(take | ref)) return -1;  // every way in flight, pinned or being written back
+      const uint32_t full = (1u << ways) - 1u;
+      // masks seen from the hand: bit i is way (h + i) mod ways
+      auto from_hand = [&](uint32_t m) { return ((m >> h) | (m << (ways - h))) & full; };
+      auto to_ways = [&](uint32_t m) { return ((m << h) | (m >> (ways - h))) & full; };
+      uint32_t rt = from_hand(take), rr = from_hand(ref), dist, clear, steps;
+      if (rt) {  // first pass: the bits of the ref ways before the victim are cleared
+        dist = (uint32_t)__ffs(rt) - 1;
+        clear = to_ways(rr & ((1u << dist) - 1u));
+        steps = dist + 1;
+      } else {   // second pass: every bit was cleared; the first ref way is the victim
+        dist = (uint32_t)__ffs(rr) - 1;
+        clear = ref;
+        steps = ways + dist + 1;
+      }
+      const uint32_t v = (h + dist) % ways;
+      clear &= ~(1u << v);
+      uint64_t tv = t[0];  // the claim expects the tag as read (its bit untouched)
+#pragma unroll
+      for (uint32_t w = 1; w < 8; ++w)
+        if (w == v) tv = t[w];
+      const bool inval = tag_state(tv) == ST_INVALID;
+      if (tag_state(tv) == ST_MODIFIED) {
+        sh_wb = sh_insert(d, tag_page(tv), SH_WRITE);
+        if (sh_wb < 0) return -1;
+      }
+      if (atomicCAS(&d.tag[base + v], (unsigned long long)tv, (unsigned long long)claimed) == tv) {
+        atomicAdd(&d.hand[set], steps);
+#pragma unroll
+        for (uint32_t w = 0; w < 8; ++w)
+          if ((clear >> w) & 1u) atomicAnd(&d.tag[base + w], ~TAG_REF);
+        old = inval ? 0 : tv;
+        return v;
+      }
+      if (sh_wb >= 0) {
+        sh_remove(d, (uint64_t)sh_wb);
+        sh_wb = -1;
+      }
+    }
+    return -1;
+  }
+  // wider sets: the sweep step by step on the live tags
+  for (uint32_t w = 0; w < ways; ++w) {
+    uint64_t t = ld_rlx64(&d.tag[base + w]);
+    if (t == 0 && atomicCAS(&d.tag[base + w], 0ull, (unsigned long long)claimed) == 0ull) {
+      old = 0;
+      return w;
+    }
+  }
+  for (uint32_t step = 0; step < 2 * ways + 1; ++step) {
+    uint32_t w = atomicAdd(&d.hand[set], 1u) % ways;
+    uint64_t t = ld_rlx64(&d.tag[base + w]);
+    uint64_t st = tag_state(t);
+    if (st == ST_INVALID) {
+      if ((t & PIN_MASK) == 0 && atomicCAS(&d.tag[base + w], (unsigned long long)t, (unsigned long long)claimed) == t) {
+        old = 0;
+        return w;
+      }
+      continue;
+    }
+    if (st == ST_BUSY || (t & (PIN_MASK | TAG_WB))) continue;
+    if (clock && (t & TAG_REF)) {
+      atomicAnd(&d.tag[base + w], ~TAG_REF);
+      continue;
+    }
+    if (st == ST_MODIFIED) {
+      sh_wb = sh_insert(d, tag_page(t), SH_WRITE);
+      if (sh_wb < 0) continue;
+    }
+    if (atomicCAS(&d.tag[base + w], (unsigned long long)t, (unsigned long long)claimed) == t) {
+      old = t;
+      return w;
+    }
+    if (sh_wb >= 0) {
+      sh_remove(d, (uint64_t)sh_wb);
+      sh_wb = -1;
+    }
+  }
+  return -1;
+}
+
 static __device__ int cache_miss(const Dev &d, uint64_t page, uint32_t q0, uint32_t &line, Issued &is,
                           bool fill = true, int64_t sh_own = -1, bool pf = false) {
   int64_t sh = sh_own;
@@ -664,42 +799,9 @@ static __device__ int cache_miss(const Dev &d, uint64_t page, uint32_t q0, uint3
   }
   uint32_t set = set_of(page, d.sets);
   uint64_t base = (uint64_t)set * d.ways;
-  uint64_t claimed = tag_make(page, ST_BUSY, true);
-  int64_t victim = -1;
   uint64_t old = 0;
   int64_t sh_wb = -1;
-  for (uint32_t w = 0; w < d.ways && victim < 0; ++w) {
-    uint64_t t = ld_rlx64(&d.tag[base + w]);
-    if (t == 0 && atomicCAS(&d.tag[base + w], 0ull, (unsigned long long)claimed) == 0ull) victim = w;
-  }
-  for (uint32_t step = 0; victim < 0 && step < 2 * d.ways + 1; ++step) {
-    uint32_t w = atomicAdd(&d.hand[set], 1u) % d.ways;
-    uint64_t t = ld_rlx64(&d.tag[base + w]);
-    uint64_t st = tag_state(t);
-    if (st == ST_INVALID) {
-      if ((t & PIN_MASK) == 0 && atomicCAS(&d.tag[base + w], (unsigned long long)t, (unsigned long long)claimed) == t) {
-        victim = w;
-        old = 0;
-      }
-      continue;
-    }
-    if (st == ST_BUSY || (t & (PIN_MASK | TAG_WB))) continue;
-    if ((t & TAG_REF) && d.policy == kPolicyClock) {
-      atomicAnd(&d.tag[base + w], ~TAG_REF);
-      continue;
-    }
-    if (st == ST_MODIFIED) {
-      sh_wb = sh_insert(d, tag_page(t), SH_WRITE);
-      if (sh_wb < 0) continue;
-    }
-    if (atomicCAS(&d.tag[base + w], (unsigned long long)t, (unsigned long long)claimed) == t) {
-      victim = w;
-      old = t;
-    } else if (sh_wb >= 0) {
-      sh_remove(d, (uint64_t)sh_wb);
-      sh_wb = -1;
-    }
-  }
+  int64_t victim = pick_victim(d, set, tag_make(page, ST_BUSY, true), old, sh_wb);
   if (victim < 0) {
     if (fill) sh_remove(d, (uint64_t)sh);
     atomicAdd(stat_ptr(d, S_EAGAIN), 1ull);
@@ -741,11 +843,11 @@ static __device__ int cache_miss(const Dev &d, uint64_t page, uint32_t q0, uint3
     is.q = 0xFFFFFFFFu;  // nothing to ring
     return M_ISSUED;
   }
+  // the read's token + 1 (0 = none yet), for threads that find the page in flight
+  // (Sec. 3.4 case (c)); the commit's release publishes it
+  st_rlx64(&d.sh_val[sh], (((uint64_t)q << 48) | ((uint64_t)slot << 32) | ticket) + 1);
   sq_commit(d, q, slot, ticket, OP_READ, (uint64_t)line_ptr(d, line), page,
             ctx_make(CTX_FILL, (uint32_t)sh, line));
-  // the read's token + 1 (0 = none yet), for threads that find the page in flight
-  // (Sec. 3.4 case (c))
-  st_rel64(&d.sh_val[sh], (((uint64_t)q << 48) | ((uint64_t)slot << 32) | ticket) + 1);
   atomicAdd(stat_ptr(d, S_MISSES), 1ull);
   is.slot = slot;
   is.ticket = ticket;
@@ -1228,10 +1330,14 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 constexpr uint32_t kEmuBatch = 2;
 constexpr uint64_t kEmuSlackNs = 16000;
 
-static __device__ uint32_t emu_serve(const Dev &d, uint32_t q) {
+// Returns the number of commands served, or kEmuDevFull when commands were due but
+// their device was booked.  block_dev: a device this call may not book (a demand
+// command of the same engine pass is waiting for it), ~0u for none.
+constexpr uint32_t kEmuDevFull = 0x80000000u;
+static __device__ uint32_t emu_serve(const Dev &d, uint32_t q, uint32_t block_dev = ~0u) {
   unsigned l = lane_id();
   uint32_t *es = &d.emu[q * 4];
-  uint32_t f = 0, k = 0;
+  uint32_t f = 0, k = 0, full = 0;
   uint64_t now = gtimer();
   const uint32_t dv = d.ndev > 1 ? q % d.ndev : 0u;  // the device this queue belongs to
   const bool model = d.lat_ns || d.ns_per_page || d.ns_rd_dev || d.ns_wr_dev;
@@ -1268,6 +1374,10 @@ static __device__ uint32_t emu_serve(const Dev &d, uint32_t q) {
         if (now < arr + d.lat_ns) break;
         ++k;
       }
+      if (k && dv == block_dev) {
+        k = 0;
+        full = kEmuDevFull;
+      }
       // Throughput: the batch is booked on the queue's pipe and on its device when each
       // is free (reads and writes take device time of their own).  Bookings follow each
       // other without gaps while the pipe has been idle for less than kEmuSlackNs
@@ -1296,6 +1406,7 @@ static __device__ uint32_t emu_serve(const Dev &d, uint32_t q) {
         uint64_t busy = ld_rlx64(&d.dev_busy[dv]);
         if (busy > now) {
           k = 0;
+          full = kEmuDevFull;
         } else {
           uint64_t nb = (busy + kEmuSlackNs > now ? busy : now) + dcost;
           dbooked = atomicCAS(&d.dev_busy[dv], (unsigned long long)busy, (unsigned long long)nb) == busy;
@@ -1310,7 +1421,7 @@ static __device__ uint32_t emu_serve(const Dev &d, uint32_t q) {
     }
   }
   k = __shfl_sync(kFull, k, 0);
-  if (!k) return 0;
+  if (!k) return __shfl_sync(kFull, full, 0);
   f = __shfl_sync(kFull, f, 0);
   __syncwarp();  // lane 0's acquire of the doorbell orders the SQE reads of every lane
   // command fields: lane i < k reads SQE f+i
@@ -1442,7 +1553,10 @@ static __device__ void service_loop(const Dev &d, uint32_t n_app, uint64_t deadl
     // (the doorbells and fetch counters of four windows of 32 queues are read in one
     // round trip; they only select a queue, emu_serve checks them again)
     // (demand queues first: the prefetch queues are served only when no demand queue
-    // has a command the device may take now)
+    // has a command the device may take now; a prefetch queue does not book a device
+    // that a due demand command found booked in this pass, so the device's next free
+    // turn goes to the demand command)
+    uint32_t block_dev = ~0u;
 #pragma unroll 1
     for (uint32_t cls = 0; cls < 2 && !progress; ++cls) {
       uint32_t qsel = ~0u;
@@ -1469,7 +1583,11 @@ static __device__ void service_loop(const Dev &d, uint32_t n_app, uint64_t deadl
           if (m && qsel == ~0u) qsel = base + (r + (w0 + j) * 32 + (uint32_t)(__ffs(m) - 1)) % cnt;
         }
       }
-      if (qsel != ~0u && emu_serve(d, qsel)) progress = true;
+      if (qsel != ~0u) {
+        uint32_t r = emu_serve(d, qsel, block_dev);
+        if (r == kEmuDevFull) block_dev = d.ndev > 1 ? qsel % d.ndev : 0u;
+        else if (r) progress = true;
+      }
     }
     // completion side (Alg. 1) for the queues this warp polls
     if (poll)

@@ -102,7 +102,7 @@ def test_noalloc_bfs_rejects_graph_beyond_its_scratch():
     n, off, cols, col0, total = _graph()
     with Ctx(total + (128 << 20), cache_bytes=64 * 4096, ways=8, num_queues=8, queue_depth=64) as c:
         lv = torch.empty(n, dtype=torch.int32, device=DEV)
-        too_many = 32768 * 1024   # needs 32,769 queue slots, one more than the array has
+        too_many = 131072 * 256   # needs 131,073 queue slots, one more than the array has
         with pytest.raises(ag.AgileError) as e:
             ag.agile_bfs_noalloc(c.h, 0, col0, n, too_many, 0, lv.data_ptr(), 0, ag.AGILE_SYNC, c.stream)
         assert e.value.code == ag.AGILE_EINVAL
