@@ -390,9 +390,9 @@ def run_bfs(args, torch, ag, dev, rank, world):
         "sync": {"value": work_sync / (ms_sync * 1e-3), "unit": "edges/s", "ms_per_step": ms_sync / args.steps},
         "async_over_sync": ms_sync / ms_async,
         "roofline": {"bound": "host_link", "achieved": achieved, "peak": link_peak, "unit": "GB/s",
-                     "frac": achieved / link_peak, "traffic": recorded_traffic("engine_kernel<BfsApp>"),
-                     "link_traffic": recorded_traffic("engine_kernel<BfsApp>", "link_bytes_per_launch"),
-                     "kernel": "engine_kernel<BfsApp>",
+                     "frac": achieved / link_peak, "traffic": recorded_traffic("engine_kernel<BfsAppT<false>>"),
+                     "link_traffic": recorded_traffic("engine_kernel<BfsAppT<false>>", "link_bytes_per_launch"),
+                     "kernel": "engine_kernel<BfsAppT<false>>",
                      "algorithmic_bytes_per_launch": algo_bytes,
                      "peak_source": "measured in this run: the better of a pinned host->HBM copy of 1 GiB (copy "
                                     "engine) and an SM 16-byte-load kernel over mapped pinned memory",
@@ -466,10 +466,10 @@ def run_spmv(args, torch, ag, dev, off, cols):
             st = ag.agile_stats(ctx)
             res[name] = {"entries_per_s": cols.size / t_call, "ms_per_call": t_call * 1e3,
                          "roofline": {"bound": "host_link", "achieved": algo / t_call / 1e9,
-                                      "traffic": recorded_traffic("engine_kernel<SpmvApp>"),
-                                      "link_traffic": recorded_traffic("engine_kernel<SpmvApp>",
+                                      "traffic": recorded_traffic("engine_kernel<SpmvAppT<false>>"),
+                                      "link_traffic": recorded_traffic("engine_kernel<SpmvAppT<false>>",
                                                                        "link_bytes_per_launch"),
-                                      "kernel": "engine_kernel<SpmvApp>", "algorithmic_bytes_per_launch": algo}}
+                                      "kernel": "engine_kernel<SpmvAppT<false>>", "algorithmic_bytes_per_launch": algo}}
         err = ag.agile_check(ctx)
         if err:
             raise RuntimeError(f"device error: {ag.strerror(err)}")
@@ -1159,6 +1159,10 @@ def main():
             extra("dlrm", lambda: run_dlrm(args, torch, ag, dev))
             extra("train", lambda: run_train(args, torch, ag, dev))
             extra("breakdown", lambda: run_breakdown(args, torch, ag, dev))
+            # Sec. 4.4 sensitivity sweeps (batch, queue pairs, cache size) and the BFS
+            # cache-size sweep, in the same record
+            extra("sweeps", lambda: run_sweeps(args, torch, ag, dev))
+            extra("bfs_cache_sweep", lambda: run_bfs_cache_sweep(args, torch, ag, dev))
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline_bfs(*graph)
     elif args.workload == "spmv":

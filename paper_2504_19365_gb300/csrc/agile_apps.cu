@@ -27,6 +27,8 @@ struct EmbApp {
   uint32_t n_bags;
   float *out;
   uint32_t mode;
+  // no request ahead of need: the launch uses every queue pair for demand
+  bool demand_only() const { return mode == AGILE_SYNC; }
   uint32_t ahead;  // rows requested ahead of the one being summed (ASYNC), 1..32
   uint32_t group;  // rows pinned together at most (cache-sized), 1..32
   // bags left by the resident pass: positions 0 .. *list_n - 1 name bags list[pos]
@@ -72,7 +74,7 @@ struct EmbApp {
           want = false;
         }
         bool all_hit = false;
-        if (!warp_request(d, want, row_page(r), a.q0, false, a.deadline, nullptr, nullptr, &all_hit, true))
+        if (!warp_request(d, want, row_page(r), a.q0, false, a.deadline, nullptr, nullptr, &all_hit, true, true))
           return false;
         bo.result(all_hit);
       }
@@ -272,6 +274,8 @@ struct PipeApp {
   uint32_t pooling, n_bags, n_batches, iters;
   float *out;         // [batches][bags][tables*dim]
   uint32_t mode;
+  // no request ahead of need: the launch uses every queue pair for demand
+  bool demand_only() const { return mode == AGILE_SYNC; }
   uint32_t group;     // rows pinned together at most (cache-sized), 1..32
   uint32_t ahead;     // async: rows of the warp's row stream requested ahead (cache-sized)
 
@@ -303,7 +307,7 @@ struct PipeApp {
           want = false;
         }
         bool all_hit = false;
-        if (!warp_request(d, want, row_page(k, r), a.q0, false, a.deadline, nullptr, nullptr, &all_hit, true))
+        if (!warp_request(d, want, row_page(k, r), a.q0, false, a.deadline, nullptr, nullptr, &all_hit, true, true))
           return false;
         bo.result(all_hit);
       }
@@ -421,6 +425,8 @@ struct BfsAppT {
   int32_t *level;
   unsigned long long *edges_out;
   uint32_t mode;
+  // no request ahead of need: the launch uses every queue pair for demand
+  bool demand_only() const { return mode == AGILE_SYNC; }
   HubEntry *hubq;
   uint32_t hub_cap;
   uint32_t *vis;  // visited bitmap: bit u set once level[u] is set (read through L1, may lag)
@@ -841,6 +847,8 @@ struct SpmvAppT {
   float *y;
   unsigned long long *entries_out;
   uint32_t mode;
+  // no request ahead of need: the launch uses every queue pair for demand
+  bool demand_only() const { return mode == AGILE_SYNC; }
   HubEntry *hubq;
   uint32_t hub_cap;
   const uint8_t *h_off = nullptr, *h_col = nullptr, *h_val = nullptr;  // kDirect: the CSR in HBM
@@ -1299,12 +1307,26 @@ __global__ void __launch_bounds__(256) resident_bag_kernel(Dev d, uint64_t page0
   const uint32_t nf4 = dim / 4;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   constexpr int RB = MF4 >= 4 ? 2 : 16 / MF4;  // rows whose loads are in flight together
-  for (uint64_t b = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; b < n_bags; b += nw) {
-    int64_t s = off[b], e = off[b + 1];
-    int64_t cnt = e - s;
+  // software pipeline over the warp's bags: the offsets of the next bag are loaded
+  // before this bag's tags, its indices before this bag's rows
+  uint64_t b = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t s = 0, e = 0;
+  uint64_t r = 0;
+  if (b < n_bags) {
+    s = off[b];
+    e = off[b + 1];
+    if ((int64_t)l < e - s && e - s <= 32) r = (uint64_t)idx[s + l];
+  }
+  for (; b < n_bags; b += nw) {
+    const uint64_t bn = b + nw;
+    int64_t sn = 0, en = 0;
+    if (bn < n_bags) {
+      sn = off[bn];
+      en = off[bn + 1];
+    }
+    const int64_t cnt = e - s;
     bool ok = cnt >= 0 && cnt <= 32;
     bool want = ok && (int64_t)l < cnt;
-    uint64_t r = want ? (uint64_t)idx[s + l] : 0;
     if (want && r >= rows) ok = false;
     uint64_t byte = (want ? r : 0) * dim * 4;
     uint64_t page = page0 + byte / kPage;
@@ -1317,59 +1339,76 @@ __global__ void __launch_bounds__(256) resident_bag_kernel(Dev d, uint64_t page0
     if (leader) {
       hit = false;
       uint64_t base = (uint64_t)set_of(page, d.sets) * d.ways;
-      for (uint32_t w = 0; w < d.ways; ++w) {
-        uint64_t t = ld_rlx64(&d.tag[base + w]);
-        uint64_t st = tag_state(t);
-        if ((st == ST_READY || st == ST_MODIFIED) && tag_page(t) == page) {
-          line = (uint32_t)(base + w);
-          hit = true;
-          if (!(t & TAG_REF)) atomicOr(&d.tag[line], TAG_REF);
-          break;
-        }
-      }
-    }
-    bool all = __all_sync(kFull, __all_sync(kFull, ok) && hit);
-    if (!all) {
-      if (l == 0) list[atomicAdd(list_n, 1u)] = (uint32_t)b;
-      continue;
-    }
-    stat_warp(d, S_HITS, leader ? 1u : 0u);
-    stat_warp(d, S_WARP_COALESCED, (want && !leader) ? 1u : 0u);
-    uint32_t myline = __shfl_sync(kFull, line, lead & 31);
-    float4 acc[MF4];
-#pragma unroll
-    for (int c = 0; c < MF4; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (uint32_t j0 = 0; j0 < (uint32_t)cnt; j0 += RB) {
-      float4 v[RB][MF4];
-#pragma unroll
-      for (int jj = 0; jj < RB; ++jj) {
-        uint32_t lj = __shfl_sync(kFull, myline, (j0 + jj) & 31);
-        uint32_t oj = __shfl_sync(kFull, in, (j0 + jj) & 31);
-        const uint8_t *rowp = line_ptr(d, lj) + oj;
-#pragma unroll
-        for (int c = 0; c < MF4; ++c) {
-          uint32_t col = l + 32 * c;
-          v[jj][c] = (j0 + jj < (uint32_t)cnt && col < nf4) ? ld_cg_f4(rowp + 16 * col)
-                                                           : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-      }
-#pragma unroll
-      for (int jj = 0; jj < RB; ++jj) {
-        if (j0 + jj < (uint32_t)cnt) {
-#pragma unroll
-          for (int c = 0; c < MF4; ++c) {
-            acc[c].x = __fadd_rn(acc[c].x, v[jj][c].x);
-            acc[c].y = __fadd_rn(acc[c].y, v[jj][c].y);
-            acc[c].z = __fadd_rn(acc[c].z, v[jj][c].z);
-            acc[c].w = __fadd_rn(acc[c].w, v[jj][c].w);
+      uint64_t t = 0;
+      int w = -1;
+      if (d.ways == 8) {  // the set's tags in one round trip
+        uint64_t pre[8];
+        ld_tags8(&d.tag[base], pre);
+        w = match_ready8(pre, page, t);
+      } else {
+        for (uint32_t k = 0; k < d.ways && w < 0; ++k) {
+          uint64_t tk = ld_rlx64(&d.tag[base + k]);
+          uint64_t st = tag_state(tk);
+          if ((st == ST_READY || st == ST_MODIFIED) && tag_page(tk) == page) {
+            w = (int)k;
+            t = tk;
           }
         }
       }
+      if (w >= 0) {
+        line = (uint32_t)(base + w);
+        hit = true;
+        if (!(t & TAG_REF)) atomicOr(&d.tag[line], TAG_REF);
+      }
     }
-    float4 *o = (float4 *)(out + b * dim);
+    // the next bag's indices (its offsets have arrived while the tags were read)
+    uint64_t rn = 0;
+    if (bn < n_bags && (int64_t)l < en - sn && en - sn <= 32) rn = (uint64_t)idx[sn + l];
+    bool all = __all_sync(kFull, __all_sync(kFull, ok) && hit);
+    if (!all) {
+      if (l == 0) list[atomicAdd(list_n, 1u)] = (uint32_t)b;
+    } else {
+      stat_warp(d, S_HITS, leader ? 1u : 0u);
+      stat_warp(d, S_WARP_COALESCED, (want && !leader) ? 1u : 0u);
+      uint32_t myline = __shfl_sync(kFull, line, lead & 31);
+      float4 acc[MF4];
 #pragma unroll
-    for (int c = 0; c < MF4; ++c)
-      if (l + 32 * c < nf4) o[l + 32 * c] = acc[c];
+      for (int c = 0; c < MF4; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (uint32_t j0 = 0; j0 < (uint32_t)cnt; j0 += RB) {
+        float4 v[RB][MF4];
+#pragma unroll
+        for (int jj = 0; jj < RB; ++jj) {
+          uint32_t lj = __shfl_sync(kFull, myline, (j0 + jj) & 31);
+          uint32_t oj = __shfl_sync(kFull, in, (j0 + jj) & 31);
+          const uint8_t *rowp = line_ptr(d, lj) + oj;
+#pragma unroll
+          for (int c = 0; c < MF4; ++c) {
+            uint32_t col = l + 32 * c;
+            v[jj][c] = (j0 + jj < (uint32_t)cnt && col < nf4) ? ld_cg_f4(rowp + 16 * col)
+                                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        }
+#pragma unroll
+        for (int jj = 0; jj < RB; ++jj) {
+          if (j0 + jj < (uint32_t)cnt) {
+#pragma unroll
+            for (int c = 0; c < MF4; ++c) {
+              acc[c].x = __fadd_rn(acc[c].x, v[jj][c].x);
+              acc[c].y = __fadd_rn(acc[c].y, v[jj][c].y);
+              acc[c].z = __fadd_rn(acc[c].z, v[jj][c].z);
+              acc[c].w = __fadd_rn(acc[c].w, v[jj][c].w);
+            }
+          }
+        }
+      }
+      float4 *o = (float4 *)(out + b * dim);
+#pragma unroll
+      for (int c = 0; c < MF4; ++c)
+        if (l + 32 * c < nf4) o[l + 32 * c] = acc[c];
+    }
+    s = sn;
+    e = en;
+    r = rn;
   }
 }
 
@@ -1378,8 +1417,8 @@ __global__ void __launch_bounds__(256) resident_bag_kernel(Dev d, uint64_t page0
 // path's ceiling and the "kernel time" of its breakdown.  A warp per bag (bags
 // b, b + W, ...); lane l adds the float4 columns l, l + 32, ... of the bag's rows in
 // increasing index order (FP32, no fusion: the cached path's bits).  The rows of up to
-// 32 indices are loaded before the first add, and the next bag's indices are read while
-// they fly.
+// 16 indices are loaded before the first add, and the next bag's offsets are read while
+// this bag's loads fly.
 template <int MF4>
 __global__ void __launch_bounds__(256) hbm_bag_kernel(const float *table, uint32_t rows, uint32_t dim,
                                                       const int64_t *idx, const int64_t *off, uint32_t n_bags,
@@ -1389,8 +1428,17 @@ __global__ void __launch_bounds__(256) hbm_bag_kernel(const float *table, uint32
   const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   constexpr int RB = MF4 >= 4 ? 4 : 16 / MF4;  // rows whose loads are in flight together
+  int64_t sn = 0, en = 0;
+  if (warp < n_bags) {
+    sn = off[warp];
+    en = off[warp + 1];
+  }
   for (uint64_t b = warp; b < n_bags; b += nw) {
-    int64_t s = off[b], e = off[b + 1];
+    const int64_t s = sn, e = en;
+    if (b + nw < n_bags) {  // the next bag's offsets, in flight with this bag's loads
+      sn = off[b + nw];
+      en = off[b + nw + 1];
+    }
     float4 acc[MF4];
 #pragma unroll
     for (int c = 0; c < MF4; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);

@@ -2,6 +2,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+#include <utility>
+
 #include <cstdio>
 #include <vector>
 
@@ -90,6 +93,14 @@ static __global__ void run_reset_kernel(RunState *r) {
 
 // `active`: application warps the call wants (0 = every app warp of the grid); the
 // context's app_warps setting overrides it.
+// An application that issues no request ahead of need in this call says so with
+//   bool demand_only() const;
+// its launch then spreads demand requests over every queue pair (no prefetch class).
+template <class T, class = void>
+struct has_demand_only : std::false_type {};
+template <class T>
+struct has_demand_only<T, std::void_t<decltype(std::declval<const T &>().demand_only())>> : std::true_type {};
+
 template <class App>
 int launch_engine(agile_ctx *c, const App &app, void *stream, uint32_t active = 0) {
   cudaStream_t s = as_stream(stream);
@@ -101,6 +112,9 @@ int launch_engine(agile_ctx *c, const App &app, void *stream, uint32_t active = 
   Dev d = c->dev;
   d.app_active = c->cfg.app_warps ? c->cfg.app_warps : active;
   if (d.extra_engines == 0xFFFFFFFFu) d.extra_engines = (uint32_t)grid;  // default: one per CTA
+  if constexpr (has_demand_only<App>::value) {
+    if (app.demand_only()) d.Qp = 0;
+  }
   App a = app;
   void *args[] = {(void *)&d, (void *)&a};
   AGILE_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)engine_kernel<App>, dim3(grid), dim3(kThreads),

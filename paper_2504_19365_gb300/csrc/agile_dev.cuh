@@ -365,7 +365,10 @@ __device__ __forceinline__ bool sq_reserve_dev(const Dev &d, uint32_t q0, uint32
   const uint32_t cnt = d.Qp ? (pf ? d.Qp : d.Q - d.Qp) : d.Q;
   const uint32_t per = cnt / nd;  // queues of one device in the class
   uint32_t k0 = (q0 / nd) % per;
-  for (uint32_t k = 0; k < per; ++k) {
+  // a request made ahead of need tries two queues: when they are full the device is
+  // saturated and the request is dropped (a hint), not spread over every queue
+  const uint32_t tries = pf ? min(per, 2u) : per;
+  for (uint32_t k = 0; k < tries; ++k) {
     uint32_t kk = k0 + k;
     if (kk >= per) kk -= per;
     uint32_t qq = base + kk * nd + dv;
@@ -376,6 +379,18 @@ __device__ __forceinline__ bool sq_reserve_dev(const Dev &d, uint32_t q0, uint32
   }
   atomicAdd(stat_ptr(d, S_SQ_FULL), 1ull);
   return false;
+}
+
+// The first queue sq_reserve_dev tries for a request of this class holds more than
+// 3/4 of its depth in flight: a request made ahead of need is then dropped before it
+// claims a line (one load instead of a claim, a failed reservation and an unclaim).
+__device__ __forceinline__ bool sq_crowded(const Dev &d, uint32_t q0, uint32_t dv, bool pf) {
+  const uint32_t nd = d.ndev > 1 ? d.ndev : 1u;
+  const uint32_t base = pf && d.Qp ? d.Q - d.Qp : 0u;
+  const uint32_t cnt = d.Qp ? (pf ? d.Qp : d.Q - d.Qp) : d.Q;
+  const uint32_t per = cnt / nd;
+  const uint32_t qq = base + ((q0 / nd) % per) * nd + dv;
+  return (uint32_t)(ld_rlx64(&d.sq_resv[qq]) >> 32) > (d.depth - 1) / 4 * 3;
 }
 
 // Alg. 2, enqueue_cmd + update_SQE: write the 64-byte command, then publish the slot
@@ -534,15 +549,46 @@ __device__ __forceinline__ void ld_tags8(const unsigned long long *p, uint64_t t
     asm volatile("ld.global.cg.v2.u64 {%0,%1}, [%2];" : "=l"(t[2 * k]), "=l"(t[2 * k + 1]) : "l"(p + 2 * k) : "memory");
 }
 
+// The way of an 8-way tag copy that holds `page` READY or MODIFIED (its tag in t), or
+// -1; unrolled, so the copy stays in registers.
+__device__ __forceinline__ int match_ready8(const uint64_t pre[8], uint64_t page, uint64_t &t) {
+  int w = -1;
+#pragma unroll
+  for (int k = 7; k >= 0; --k) {
+    uint64_t st = tag_state(pre[k]);
+    if ((st == ST_READY || st == ST_MODIFIED) && tag_page(pre[k]) == page) {
+      w = k;
+      t = pre[k];
+    }
+  }
+  return w;
+}
+
 __device__ __forceinline__ int cache_probe(const Dev &d, uint64_t page, bool pin, uint32_t &line) {
   uint64_t base = (uint64_t)set_of(page, d.sets) * d.ways;
-  uint64_t pre[8];
-  const bool vec = d.ways == 8;  // sets of 8 ways are 64-byte aligned: read them at once
-  if (vec) ld_tags8(&d.tag[base], pre);
-  for (uint32_t w = 0; w < d.ways; ++w) {
-    uint64_t t = vec ? pre[w & 7] : ld_rlx64(&d.tag[base + w]);
+  uint64_t t = 0;
+  int wsel = -1;
+  if (d.ways == 8) {  // sets of 8 ways are 64-byte aligned: read them at once
+    uint64_t pre[8];
+    ld_tags8(&d.tag[base], pre);
+#pragma unroll
+    for (int k = 7; k >= 0; --k)
+      if (tag_state(pre[k]) != ST_INVALID && tag_page(pre[k]) == page) {
+        wsel = k;
+        t = pre[k];
+      }
+  } else {
+    for (uint32_t k = 0; k < d.ways && wsel < 0; ++k) {
+      uint64_t tk = ld_rlx64(&d.tag[base + k]);
+      if (tag_state(tk) != ST_INVALID && tag_page(tk) == page) {
+        wsel = (int)k;
+        t = tk;
+      }
+    }
+  }
+  if (wsel >= 0) {
+    const uint32_t w = (uint32_t)wsel;
     uint64_t st = tag_state(t);
-    if (st == ST_INVALID || tag_page(t) != page) continue;
     line = (uint32_t)(base + w);
     if (st == ST_BUSY) return P_BUSY;
     if (!pin) {
@@ -652,97 +698,16 @@ static __device__ __noinline__ int cache_miss_split(const Dev &d, uint64_t page,
 // Victim search of a miss in `set` (Sec. 3.4 cases (b) and (d)): the lowest way with
 // an INVALID, unpinned tag, else the clock sweep from the set's hand (a way whose
 // reference bit is set has it cleared and is passed; BUSY, pinned and written-back
-// ways are passed; under FIFO no bit is looked at).  The chosen way is claimed by
-// compare-and-swap from the tag that was read, as BUSY for the new page (`claimed`).
-// Returns the way (old = its tag before, 0 when it was INVALID; sh_wb = the Share
-// Table entry of the write-back of a MODIFIED victim) or -1.
-//
-// Sets of at most 8 ways are read once (tags and hand) and the sweep runs on that
-// copy: the hand advance and the cleared reference bits are published only once the
-// claim has succeeded (fire-and-forget atomics), and a failed claim reads the set
-// again.  With one request in flight the decisions are those of the stepwise sweep.
+// ways are passed; under FIFO no bit is looked at).  Each step of the hand is a
+// fetch-and-add, so misses racing in one set sweep different ways.  The chosen way is
+// claimed by compare-and-swap from the tag that was read, as BUSY for the new page
+// (`claimed`).  Returns the way (old = its tag before, 0 when it was INVALID; sh_wb =
+// the Share Table entry of the write-back of a MODIFIED victim) or -1.  Kept out of
+// line: the miss path's registers stay out of the callers' loops.
 static __device__ __noinline__ int64_t pick_victim(const Dev &d, uint32_t set, uint64_t claimed, uint64_t &old,
                                                    int64_t &sh_wb) {
   const uint32_t ways = d.ways;
   const uint64_t base = (uint64_t)set * ways;
-  const bool clock = d.policy == kPolicyClock;
-  if (ways <= 8) {
-#pragma unroll 1
-    for (int attempt = 0; attempt < 8; ++attempt) {
-      uint64_t t[8];
-      if (ways == 8) {
-        ld_tags8(&d.tag[base], t);
-      } else {
-#pragma unroll
-        for (uint32_t w = 0; w < 8; ++w) t[w] = w < ways ? ld_rlx64(&d.tag[base + w]) : 0ull;
-      }
-      const uint32_t h = ld_rlx32(&d.hand[set]) % ways;
-      // (b) the lowest free way
-#pragma unroll
-      for (uint32_t w = 0; w < 8; ++w)
-        if (w < ways && t[w] == 0 &&
-            atomicCAS(&d.tag[base + w], 0ull, (unsigned long long)claimed) == 0ull) {
-          old = 0;
-          return w;
-        }
-      // (d) the sweep as bit masks over the ways: `take` ways end it when the hand
-      // reaches them (INVALID and unpinned, or evictable with a clear bit); `ref`
-      // ways are passed once with their bit cleared and end the second pass.
-      uint32_t take = 0, ref = 0;
-#pragma unroll
-      for (uint32_t w = 0; w < 8; ++w) {
-        if (w >= ways) continue;
-        uint64_t st = tag_state(t[w]);
-        bool pinned = (t[w] & PIN_MASK) != 0;
-        if (st == ST_INVALID) {
-          if (!pinned) take |= 1u << w;
-        } else if (st != ST_BUSY && !pinned && !(t[w] & TAG_WB)) {
-          if (clock && (t[w] & TAG_REF)) ref |= 1u << w;
-          else take |= 1u << w;
-        }
-      }
-      if (!(take | ref)) return -1;  // every way in flight, pinned or being written back
-      const uint32_t full = (1u << ways) - 1u;
-      // masks seen from the hand: bit i is way (h + i) mod ways
-      auto from_hand = [&](uint32_t m) { return ((m >> h) | (m << (ways - h))) & full; };
-      auto to_ways = [&](uint32_t m) { return ((m << h) | (m >> (ways - h))) & full; };
-      uint32_t rt = from_hand(take), rr = from_hand(ref), dist, clear, steps;
-      if (rt) {  // first pass: the bits of the ref ways before the victim are cleared
-        dist = (uint32_t)__ffs(rt) - 1;
-        clear = to_ways(rr & ((1u << dist) - 1u));
-        steps = dist + 1;
-      } else {   // second pass: every bit was cleared; the first ref way is the victim
-        dist = (uint32_t)__ffs(rr) - 1;
-        clear = ref;
-        steps = ways + dist + 1;
-      }
-      const uint32_t v = (h + dist) % ways;
-      clear &= ~(1u << v);
-      uint64_t tv = t[0];  // the claim expects the tag as read (its bit untouched)
-#pragma unroll
-      for (uint32_t w = 1; w < 8; ++w)
-        if (w == v) tv = t[w];
-      const bool inval = tag_state(tv) == ST_INVALID;
-      if (tag_state(tv) == ST_MODIFIED) {
-        sh_wb = sh_insert(d, tag_page(tv), SH_WRITE);
-        if (sh_wb < 0) return -1;
-      }
-      if (atomicCAS(&d.tag[base + v], (unsigned long long)tv, (unsigned long long)claimed) == tv) {
-        atomicAdd(&d.hand[set], steps);
-#pragma unroll
-        for (uint32_t w = 0; w < 8; ++w)
-          if ((clear >> w) & 1u) atomicAnd(&d.tag[base + w], ~TAG_REF);
-        old = inval ? 0 : tv;
-        return v;
-      }
-      if (sh_wb >= 0) {
-        sh_remove(d, (uint64_t)sh_wb);
-        sh_wb = -1;
-      }
-    }
-    return -1;
-  }
-  // wider sets: the sweep step by step on the live tags
   for (uint32_t w = 0; w < ways; ++w) {
     uint64_t t = ld_rlx64(&d.tag[base + w]);
     if (t == 0 && atomicCAS(&d.tag[base + w], 0ull, (unsigned long long)claimed) == 0ull) {
@@ -762,7 +727,7 @@ static __device__ __noinline__ int64_t pick_victim(const Dev &d, uint32_t set, u
       continue;
     }
     if (st == ST_BUSY || (t & (PIN_MASK | TAG_WB))) continue;
-    if (clock && (t & TAG_REF)) {
+    if (d.policy == kPolicyClock && (t & TAG_REF)) {
       atomicAnd(&d.tag[base + w], ~TAG_REF);
       continue;
     }
@@ -868,12 +833,14 @@ __device__ __forceinline__ uint64_t make_token(uint32_t q, uint32_t slot, uint32
 // wait=true it returns once every page is READY (no pins are held while waiting).
 // Returns false on timeout/abort.  `tok` (leaders) receives the token of the read the
 // lane itself issued, AGILE_TOKEN_HIT otherwise.
-// `all_hit` (optional) receives, in every lane, whether every leader's page was
-// READY at its first probe (the request had nothing to do).
+// `all_hit` (optional) receives, in every lane, whether no leader's page went to the
+// device: each was READY at its first probe, or (hint) its request was dropped.
 // `pf`: the pages are requested ahead of need (prefetch queues, served after demand).
+// `hint`: a speculative request of an application's lookahead, dropped (no retry) when
+// its first queue is crowded or no queue has room -- the device is saturated.
 static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint32_t q0, bool wait,
                              uint64_t deadline, uint64_t *tok = nullptr, int *code = nullptr,
-                             bool *all_hit = nullptr, bool pf = false) {
+                             bool *all_hit = nullptr, bool pf = false, bool hint = false) {
   unsigned grp = __match_any_sync(kFull, want ? page : ~0ull);
   int lead_lane = __ffs(grp) - 1;
   bool leader = want && lead_lane == (int)lane_id();
@@ -899,6 +866,9 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
       } else if (pr == P_BUSY) {
         if (first) atomicAdd(stat_ptr(d, S_BUSY_HITS), 1ull);
         if (!wait) need = false;
+      } else if (hint && !wait && sq_crowded(d, q0, dev_of_page(d, page), pf)) {
+        need = false;  // the device is saturated: drop the hint
+        first_miss = false;
       } else {
         int m = cache_miss(d, page, q0, line, is, true, -1, pf);
         ring = m == M_ISSUED;
@@ -911,8 +881,9 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
           need = false;
         } else if (m == M_BUSY) {
           if (!wait) need = false;
-        } else if (!wait && ++retries >= 4) {
+        } else if (!wait && (hint || ++retries >= 4)) {
           need = false;  // a prefetch is a hint: give up when nothing can be evicted now
+          if (hint) first_miss = false;
         }
       }
     }
@@ -1005,7 +976,8 @@ static __device__ bool warp_pin_page(const Dev &d, uint64_t page, uint32_t q0, u
 
 // Asynchronous requests ahead of use pay a probe per page even when every page is
 // already resident.  A warp whose requests keep finding nothing to do requests less
-// often: after a round in which every page was resident it skips the next `span`
+// often: after a round in which every page was resident (or every request was dropped
+// because the device was saturated) it skips the next `span`
 // rounds (span 1, 3, 7, ... up to 63), and any round that found work, or any miss met
 // later by the warp's own gather, brings it back to every round.  Skipped pages are
 // fetched when used, as in synchronous mode.

@@ -33,6 +33,8 @@ struct ReadApp {
   uint8_t *dst;
   uint64_t *tok;
   uint32_t mode;
+  // no request ahead of need: the launch uses every queue pair for demand
+  bool demand_only() const { return mode == AGILE_SYNC && !prefetch_only; }
   int prefetch_only;
   __device__ void run(const Dev &d, const AppCtx &a) const {
     unsigned l = lane_id();

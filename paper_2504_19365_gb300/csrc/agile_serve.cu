@@ -87,6 +87,8 @@ struct ServeApp {
   uint32_t ring_n;
   uint64_t budget;              // lines that admitted requests may hold together
   uint32_t mode;
+  // serving requests only what it sums: every queue pair carries demand
+  bool demand_only() const { return true; }
   uint32_t group;
 
   __device__ void schedule(const Dev &d, const AppCtx &a) const {

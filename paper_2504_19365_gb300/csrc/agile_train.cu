@@ -83,6 +83,8 @@ struct BackwardApp {
   float lr;
   float *grad_table;
   uint32_t mode;
+  // no request ahead of need: the launch uses every queue pair for demand
+  bool demand_only() const { return mode == AGILE_SYNC; }
 
   __device__ __forceinline__ uint32_t row_at(uint64_t j) const { return (uint32_t)(keys[j] >> 32); }
 
@@ -90,7 +92,7 @@ struct BackwardApp {
     uint64_t j = base + lane_id();
     bool head = j < n && (j == 0 || row_at(j) != row_at(j - 1));
     uint64_t pg = head ? page0 + ((uint64_t)row_at(j) * dim * 4) / kPage : 0;
-    return warp_request(d, head, pg, a.q0, false, a.deadline, nullptr, nullptr, nullptr, true);
+    return warp_request(d, head, pg, a.q0, false, a.deadline, nullptr, nullptr, nullptr, true, true);
   }
 
   __device__ void run(const Dev &d, const AppCtx &a) const {

@@ -7,7 +7,8 @@ the device figures the model stands in for (about 3.7 GB/s of 4 KiB random reads
 2.2 GB/s of writes per SSD, requests interleaved over the SSDs).  Here:
   - no command is taken before the configured latency has passed since the device saw
     its doorbell;
-  - a queue capped at R GB/s serves its pages at R, within 10 %, when it is kept full;
+  - a queue capped at R GB/s never serves faster than R, and serves at R, within 10 %,
+    while it has commands waiting;
   - n devices capped at R each serve about n R together, and a page's command always
     goes to a queue of the page's device (page p on device p mod n);
   - write-backs that leave for another device than the read that replaces them keep
@@ -72,14 +73,22 @@ def test_queue_throughput_cap():
         _read(c, pages)
         tr, n = ag.agile_trace(c.h, 4096)
         assert n == npages
+        per_page = 4096 / cap   # ns
         for k in range(q):
-            t = np.sort(tr["t_start"][tr["q"] == k]).astype(np.float64)
+            sel = tr[tr["q"] == k]
+            order = np.argsort(sel["t_start"], kind="stable")
+            t = sel["t_start"][order].astype(np.float64)
+            seen = sel["t_seen"][order].astype(np.float64)
             assert t.size > 100
-            # while the queue is kept full: between its 10th and 90th percentile commands
-            # (the ramp-up and the drain at the ends are not at the cap)
-            a, b = int(0.1 * t.size), int(0.9 * t.size)
-            rate = (b - a) * 4096 / (t[b] - t[a])   # bytes per ns = GB/s
-            assert 0.9 * cap <= rate <= 1.1 * cap, (k, rate)
+            # never faster than the cap over the whole run (one slack window of 16 us)
+            assert (t.size - 1) * per_page <= t[-1] - t[0] + 16_000, k
+            # while the queue has work waiting (a command seen before the one ahead of it
+            # started), it is served at the cap: the mean spacing of those starts is one
+            # page time
+            back = seen[1:] <= t[:-1]
+            assert back.sum() > 50, k
+            gap = (t[1:] - t[:-1])[back].mean()
+            assert 0.9 * per_page <= gap <= 1.1 * per_page, (k, gap, per_page)
 
 
 @pytest.mark.parametrize("ndev", [1, 2, 3])
