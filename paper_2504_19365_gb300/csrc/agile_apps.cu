@@ -425,8 +425,9 @@ struct BfsAppT {
   int32_t *level;
   unsigned long long *edges_out;
   uint32_t mode;
-  // no request ahead of need: the launch uses every queue pair for demand
-  bool demand_only() const { return mode == AGILE_SYNC; }
+  // its early requests (async) are for pages the warp reads right after, never a
+  // lookahead: every queue pair carries demand in both modes
+  bool demand_only() const { return true; }
   HubEntry *hubq;
   uint32_t hub_cap;
   uint32_t *vis;  // visited bitmap: bit u set once level[u] is set (read through L1, may lag)
@@ -847,8 +848,9 @@ struct SpmvAppT {
   float *y;
   unsigned long long *entries_out;
   uint32_t mode;
-  // no request ahead of need: the launch uses every queue pair for demand
-  bool demand_only() const { return mode == AGILE_SYNC; }
+  // its early requests (async) are for pages the warp reads right after, never a
+  // lookahead: every queue pair carries demand in both modes
+  bool demand_only() const { return true; }
   HubEntry *hubq;
   uint32_t hub_cap;
   const uint8_t *h_off = nullptr, *h_col = nullptr, *h_val = nullptr;  // kDirect: the CSR in HBM
@@ -1300,13 +1302,15 @@ using SpmvApp = SpmvAppT<false>;
 // READY / MODIFIED is listed.  The sum is the engine's: rows in increasing index order,
 // FP32, no fusion.
 template <int MF4>
-__global__ void __launch_bounds__(256) resident_bag_kernel(Dev d, uint64_t page0, uint32_t rows, uint32_t dim,
+__global__ void __launch_bounds__(256, MF4 >= 8 ? 2 : 3) resident_bag_kernel(Dev d, uint64_t page0, uint32_t rows, uint32_t dim,
                                                            const int64_t *idx, const int64_t *off, uint32_t n_bags,
                                                            float *out, uint32_t *list, uint32_t *list_n) {
   const unsigned l = threadIdx.x & 31;
   const uint32_t nf4 = dim / 4;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  constexpr int RB = MF4 >= 4 ? 2 : 16 / MF4;  // rows whose loads are in flight together
+  // rows whose loads are in flight together (few registers: three CTAs an SM, two for
+  // the widest rows)
+  constexpr int RB = MF4 >= 4 ? 2 : 8 / MF4;
   // software pipeline over the warp's bags: the offsets of the next bag are loaded
   // before this bag's tags, its indices before this bag's rows
   uint64_t b = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
