@@ -73,10 +73,10 @@ struct EmbApp {
           set_error(d, AGILE_EINVAL);
           want = false;
         }
-        bool all_hit = false;
-        if (!warp_request(d, want, row_page(r), a.q0, false, a.deadline, nullptr, nullptr, &all_hit, true, true))
+        uint32_t outcome = 0;
+        if (!warp_request(d, want, row_page(r), a.q0, false, a.deadline, nullptr, nullptr, &outcome, true, true))
           return false;
-        bo.result(all_hit);
+        bo.result(outcome);
       }
       c.i += take;
       cnt -= take;
@@ -306,10 +306,10 @@ struct PipeApp {
           set_error(d, AGILE_EINVAL);
           want = false;
         }
-        bool all_hit = false;
-        if (!warp_request(d, want, row_page(k, r), a.q0, false, a.deadline, nullptr, nullptr, &all_hit, true, true))
+        uint32_t outcome = 0;
+        if (!warp_request(d, want, row_page(k, r), a.q0, false, a.deadline, nullptr, nullptr, &outcome, true, true))
           return false;
-        bo.result(all_hit);
+        bo.result(outcome);
       }
       c.q += take;
       cnt -= take;

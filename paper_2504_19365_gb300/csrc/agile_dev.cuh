@@ -833,14 +833,15 @@ __device__ __forceinline__ uint64_t make_token(uint32_t q, uint32_t slot, uint32
 // wait=true it returns once every page is READY (no pins are held while waiting).
 // Returns false on timeout/abort.  `tok` (leaders) receives the token of the read the
 // lane itself issued, AGILE_TOKEN_HIT otherwise.
-// `all_hit` (optional) receives, in every lane, whether no leader's page went to the
-// device: each was READY at its first probe, or (hint) its request was dropped.
+// `outcome` (optional) receives, in every lane, bit 0: some leader's page was not
+// READY at its first probe and its request went to the device (or was in flight);
+// bit 1: some hint was dropped because the device is saturated.
 // `pf`: the pages are requested ahead of need (prefetch queues, served after demand).
 // `hint`: a speculative request of an application's lookahead, dropped (no retry) when
 // its first queue is crowded or no queue has room -- the device is saturated.
 static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint32_t q0, bool wait,
                              uint64_t deadline, uint64_t *tok = nullptr, int *code = nullptr,
-                             bool *all_hit = nullptr, bool pf = false, bool hint = false) {
+                             uint32_t *outcome = nullptr, bool pf = false, bool hint = false) {
   unsigned grp = __match_any_sync(kFull, want ? page : ~0ull);
   int lead_lane = __ffs(grp) - 1;
   bool leader = want && lead_lane == (int)lane_id();
@@ -853,7 +854,7 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
   uint32_t retries = 0;
   if (tok && leader) *tok = ~0ull;
   if (code && leader) *code = 0;
-  bool first_miss = false;
+  bool first_miss = false, dropped = false;
   while (__any_sync(kFull, need)) {
     bool issued = false, ring = false;
     Issued is{};
@@ -869,6 +870,7 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
       } else if (hint && !wait && sq_crowded(d, q0, dev_of_page(d, page), pf)) {
         need = false;  // the device is saturated: drop the hint
         first_miss = false;
+        dropped = true;
       } else {
         int m = cache_miss(d, page, q0, line, is, true, -1, pf);
         ring = m == M_ISSUED;
@@ -883,7 +885,10 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
           if (!wait) need = false;
         } else if (!wait && (hint || ++retries >= 4)) {
           need = false;  // a prefetch is a hint: give up when nothing can be evicted now
-          if (hint) first_miss = false;
+          if (hint) {
+            first_miss = false;
+            dropped = true;
+          }
         }
       }
     }
@@ -905,7 +910,7 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
       }
     }
   }
-  if (all_hit) *all_hit = !__any_sync(kFull, first_miss);
+  if (outcome) *outcome = (__any_sync(kFull, first_miss) ? 1u : 0u) | (__any_sync(kFull, dropped) ? 2u : 0u);
   return __all_sync(kFull, ok);
 }
 
@@ -974,15 +979,17 @@ static __device__ bool warp_pin_page(const Dev &d, uint64_t page, uint32_t q0, u
   }
 }
 
-// Asynchronous requests ahead of use pay a probe per page even when every page is
-// already resident.  A warp whose requests keep finding nothing to do requests less
-// often: after a round in which every page was resident (or every request was dropped
-// because the device was saturated) it skips the next `span`
-// rounds (span 1, 3, 7, ... up to 63), and any round that found work, or any miss met
-// later by the warp's own gather, brings it back to every round.  Skipped pages are
-// fetched when used, as in synchronous mode.
+// Asynchronous requests ahead of use pay a probe per page even when they have nothing
+// to do: every page already resident, or the device saturated (the hints are dropped).
+// A warp whose lookahead keeps finding nothing to do requests less often: after such a
+// round it skips the next `span` rounds (span 1, 3, 7, ... up to 63).  A round that
+// sends work to the device brings it back to every round, and so does a miss met later
+// by the warp's own gather -- unless the last round was dropped for saturation (the
+// gather misses then because the hints were dropped, and more lookahead would only be
+// dropped again).  Skipped pages are fetched when used, as in synchronous mode.
 struct Backoff {
   uint32_t skip = 0, span = 0;
+  bool sat = false;
   __device__ __forceinline__ bool take() {  // true: request this round
     if (skip) {
       --skip;
@@ -990,15 +997,20 @@ struct Backoff {
     }
     return true;
   }
-  __device__ __forceinline__ void result(bool all_hit) {
-    if (all_hit) {
+  // outcome of warp_request: bit 0 work sent to the device, bit 1 hints dropped
+  __device__ __forceinline__ void result(uint32_t outcome) {
+    if (outcome & 1u) {
+      span = 0;
+      sat = false;
+    } else {
       span = span < 63 ? 2 * span + 1 : 63;
       skip = span;
-    } else {
-      span = 0;
+      sat = (outcome & 2u) != 0;
     }
   }
-  __device__ __forceinline__ void missed() { skip = span = 0; }
+  __device__ __forceinline__ void missed() {
+    if (!sat) skip = span = 0;
+  }
 };
 
 // what an application warp knows about its launch

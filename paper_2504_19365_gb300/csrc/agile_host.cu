@@ -34,7 +34,7 @@ struct ReadApp {
   uint64_t *tok;
   uint32_t mode;
   // no request ahead of need: the launch uses every queue pair for demand
-  bool demand_only() const { return mode == AGILE_SYNC && !prefetch_only; }
+  bool demand_only() const { return !prefetch_only; }  // reads are waited for in both modes
   int prefetch_only;
   __device__ void run(const Dev &d, const AppCtx &a) const {
     unsigned l = lane_id();
