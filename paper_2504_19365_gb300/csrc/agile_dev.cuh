@@ -833,9 +833,9 @@ __device__ __forceinline__ uint64_t make_token(uint32_t q, uint32_t slot, uint32
 // wait=true it returns once every page is READY (no pins are held while waiting).
 // Returns false on timeout/abort.  `tok` (leaders) receives the token of the read the
 // lane itself issued, AGILE_TOKEN_HIT otherwise.
-// `outcome` (optional) receives, in every lane, bit 0: some leader's page was not
-// READY at its first probe and its request went to the device (or was in flight);
-// bit 1: some hint was dropped because the device is saturated.
+// `outcome` (optional) receives, in every lane, bit 0: this call sent a read to the
+// device (a page READY or already in flight adds nothing); bit 1: some hint was
+// dropped because the device is saturated.
 // `pf`: the pages are requested ahead of need (prefetch queues, served after demand).
 // `hint`: a speculative request of an application's lookahead, dropped (no retry) when
 // its first queue is crowded or no queue has room -- the device is saturated.
@@ -854,13 +854,12 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
   uint32_t retries = 0;
   if (tok && leader) *tok = ~0ull;
   if (code && leader) *code = 0;
-  bool first_miss = false, dropped = false;
+  bool dropped = false, sent = false;
   while (__any_sync(kFull, need)) {
     bool issued = false, ring = false;
     Issued is{};
     if (need) {
       int pr = cache_probe(d, page, false, line);
-      if (first && pr != P_HIT) first_miss = true;
       if (pr == P_HIT) {
         need = false;
         if (first) atomicAdd(stat_ptr(d, S_HITS), 1ull);
@@ -869,13 +868,13 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
         if (!wait) need = false;
       } else if (hint && !wait && sq_crowded(d, q0, dev_of_page(d, page), pf)) {
         need = false;  // the device is saturated: drop the hint
-        first_miss = false;
         dropped = true;
       } else {
         int m = cache_miss(d, page, q0, line, is, true, -1, pf);
         ring = m == M_ISSUED;
         if (m == M_ISSUED) {
           issued = true;
+          sent = true;
           if (tok) *tok = make_token(is.q, is.slot, is.ticket);
           if (code) *code = is.code;
           if (!wait) need = false;
@@ -885,10 +884,7 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
           if (!wait) need = false;
         } else if (!wait && (hint || ++retries >= 4)) {
           need = false;  // a prefetch is a hint: give up when nothing can be evicted now
-          if (hint) {
-            first_miss = false;
-            dropped = true;
-          }
+          if (hint) dropped = true;
         }
       }
     }
@@ -910,7 +906,7 @@ static __device__ bool warp_request(const Dev &d, bool want, uint64_t page, uint
       }
     }
   }
-  if (outcome) *outcome = (__any_sync(kFull, first_miss) ? 1u : 0u) | (__any_sync(kFull, dropped) ? 2u : 0u);
+  if (outcome) *outcome = (__any_sync(kFull, sent) ? 1u : 0u) | (__any_sync(kFull, dropped) ? 2u : 0u);
   return __all_sync(kFull, ok);
 }
 
@@ -980,7 +976,8 @@ static __device__ bool warp_pin_page(const Dev &d, uint64_t page, uint32_t q0, u
 }
 
 // Asynchronous requests ahead of use pay a probe per page even when they have nothing
-// to do: every page already resident, or the device saturated (the hints are dropped).
+// to do: every page already resident or in flight, or the device saturated (the hints
+// are dropped).
 // A warp whose lookahead keeps finding nothing to do requests less often: after such a
 // round it skips the next `span` rounds (span 1, 3, 7, ... up to 63).  A round that
 // sends work to the device brings it back to every round, and so does a miss met later
