@@ -70,9 +70,10 @@ def csrc_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, key: str = "dram_bytes_per_launch"):
+def recorded_traffic(kernel: str, key: str = "dram_bytes_per_launch", workload: str | None = None):
     """Bytes per launch from the committed ncu summary (DRAM, or host link with
-    key="link_bytes_per_launch"), if it was taken on the current sources; else None."""
+    key="link_bytes_per_launch"), if it was taken on the current sources and on this
+    workload; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -81,7 +82,7 @@ def recorded_traffic(kernel: str, key: str = "dram_bytes_per_launch"):
         if line.startswith("#"):
             continue
         parts = dict(p.split("=", 1) for p in line.split() if "=" in p)
-        if parts.get("kernel") == kernel and parts.get("source") == cur:
+        if parts.get("kernel") == kernel and parts.get("source") == cur and parts.get("workload") == workload:
             try:
                 return float(parts[key])
             except (KeyError, ValueError):
@@ -390,8 +391,10 @@ def run_bfs(args, torch, ag, dev, rank, world):
         "sync": {"value": work_sync / (ms_sync * 1e-3), "unit": "edges/s", "ms_per_step": ms_sync / args.steps},
         "async_over_sync": ms_sync / ms_async,
         "roofline": {"bound": "host_link", "achieved": achieved, "peak": link_peak, "unit": "GB/s",
-                     "frac": achieved / link_peak, "traffic": recorded_traffic("engine_kernel<BfsAppT<false>>"),
-                     "link_traffic": recorded_traffic("engine_kernel<BfsAppT<false>>", "link_bytes_per_launch"),
+                     "frac": achieved / link_peak, "traffic": recorded_traffic("engine_kernel<BfsAppT<false>>",
+                                                                            workload=f"bfs_rmat{args.bfs_scale}"),
+                     "link_traffic": recorded_traffic("engine_kernel<BfsAppT<false>>", "link_bytes_per_launch",
+                                                      workload=f"bfs_rmat{args.bfs_scale}"),
                      "kernel": "engine_kernel<BfsAppT<false>>",
                      "algorithmic_bytes_per_launch": algo_bytes,
                      "peak_source": "measured in this run: the better of a pinned host->HBM copy of 1 GiB (copy "
@@ -466,9 +469,10 @@ def run_spmv(args, torch, ag, dev, off, cols):
             st = ag.agile_stats(ctx)
             res[name] = {"entries_per_s": cols.size / t_call, "ms_per_call": t_call * 1e3,
                          "roofline": {"bound": "host_link", "achieved": algo / t_call / 1e9,
-                                      "traffic": recorded_traffic("engine_kernel<SpmvAppT<false>>"),
+                                      "traffic": recorded_traffic("engine_kernel<SpmvAppT<false>>",
+                                                                  workload="spmv_rmat20"),
                                       "link_traffic": recorded_traffic("engine_kernel<SpmvAppT<false>>",
-                                                                       "link_bytes_per_launch"),
+                                                                       "link_bytes_per_launch", workload="spmv_rmat20"),
                                       "kernel": "engine_kernel<SpmvAppT<false>>", "algorithmic_bytes_per_launch": algo}}
         err = ag.agile_check(ctx)
         if err:
@@ -1055,7 +1059,7 @@ def run_hits(args, torch, ag, dev):
             res[name] = {"lookups_per_s": nb * pool / t, "ms_per_launch": t * 1e3, "misses": st["misses"],
                          "roofline": {"bound": "hbm", "achieved": algo / t / 1e9, "peak": HBM_PEAK, "unit": "GB/s",
                                       "frac": algo / t / 1e9 / HBM_PEAK,
-                                      "traffic": recorded_traffic("resident_bag_kernel<1>"),
+                                      "traffic": recorded_traffic("resident_bag_kernel<1>", workload="hits_1gib"),
                                       "kernel": "resident_bag_kernel<1>",
                                       "timed": "the whole call: the resident pass, then the engine launch for the "
                                                "bags it leaves (none when every page is resident)",

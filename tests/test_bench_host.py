@@ -29,16 +29,19 @@ def test_source_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
     assert bench.csrc_hash() != h0
 
 
-def test_recorded_traffic_is_keyed_to_the_source_hash(tmp_path, monkeypatch):
+def test_recorded_traffic_is_keyed_to_the_source_hash_and_workload(tmp_path, monkeypatch):
     _copy_tree(tmp_path)
     (tmp_path / "profiles").mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     h = bench.csrc_hash()
     (tmp_path / "profiles" / "ncu_traffic.txt").write_text(
         "# comment\n"
-        f"kernel=engine_kernel<BfsApp> source={h} dram_bytes_per_launch=123 link_bytes_per_launch=456\n"
-        "kernel=engine_kernel<EmbApp<1,3>> source=0000000000000000 dram_bytes_per_launch=7\n")
-    assert bench.recorded_traffic("engine_kernel<BfsApp>") == 123.0
-    assert bench.recorded_traffic("engine_kernel<BfsApp>", "link_bytes_per_launch") == 456.0
-    assert bench.recorded_traffic("engine_kernel<EmbApp<1,3>>") is None   # taken on other sources
-    assert bench.recorded_traffic("engine_kernel<SpmvApp>") is None
+        f"kernel=engine_kernel<BfsAppT<false>> workload=bfs_rmat20 source={h} dram_bytes_per_launch=123 "
+        "link_bytes_per_launch=456\n"
+        "kernel=resident_bag_kernel<1> workload=hits_1gib source=0000000000000000 dram_bytes_per_launch=7\n")
+    k = "engine_kernel<BfsAppT<false>>"
+    assert bench.recorded_traffic(k, workload="bfs_rmat20") == 123.0
+    assert bench.recorded_traffic(k, "link_bytes_per_launch", workload="bfs_rmat20") == 456.0
+    assert bench.recorded_traffic(k, workload="bfs_rmat16") is None        # another workload
+    assert bench.recorded_traffic("resident_bag_kernel<1>", workload="hits_1gib") is None   # other sources
+    assert bench.recorded_traffic("engine_kernel<SpmvAppT<false>>", workload="spmv_rmat20") is None
