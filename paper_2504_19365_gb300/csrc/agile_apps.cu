@@ -389,10 +389,13 @@ struct PipeApp {
 // the grid barrier that ends the level; the search stops when a level discovers
 // nothing.  Edges scanned = sum of the degrees of the frontier vertices of all levels.
 //   SYNC : each page (offsets, columns) is requested when needed and waited for.
-//   ASYNC: as SYNC for a warp's own vertices, and a long-list slice requests all of its
-//          pages before it is scanned, so that their fetches overlap.  (Requesting the
-//          pages of the next units ahead as well was measured slower with the cache at
-//          an eighth of the column array: those pages were evicted before their use.)
+//   ASYNC: reads are issued before they are waited for, within the work at hand: a
+//          32-vertex unit requests the list pages of all of its lanes before it scans
+//          them, a sparse chunk requests its units' list pages together, and a long-list
+//          slice requests all of its pages before it is scanned, so that their fetches
+//          overlap.  (Requesting the pages of the next units ahead as well was measured
+//          slower with the cache at an eighth of the column array: those pages were
+//          evicted before their use.)
 // A warp keeps at most one line pinned between steps (the page it read last) and lets
 // it go before it requests or waits for any other page.
 // One slice (at most kSlice entries) of a long adjacency list, queued for any warp.
@@ -681,7 +684,7 @@ struct BfsAppT {
     return warp_request_call(d, has, col_page0 + pg, a.q0, false, a.deadline);
   }
 
-  // one 32-vertex unit: every page when needed
+  // one 32-vertex unit: SYNC requests every page when needed
   __device__ bool chunk(const Dev &d, const AppCtx &a, uint32_t v0, int32_t L, uint32_t &found,
                         unsigned long long &scanned, Pin &pc) const {
     uint32_t v = v0 + lane_id();
@@ -692,7 +695,27 @@ struct BfsAppT {
     uint32_t deg = f ? (uint32_t)(e - s) : 0;
     scanned += __reduce_add_sync(kFull, deg);
     bool hub = push_hub(d, deg, s, e, L);
-    return scan_lists(d, a, s, hub ? 0 : deg, L, found, pc);
+    const uint32_t dg = hub ? 0 : deg;
+    if (!kDirect && mode == AGILE_ASYNC) {
+      // ASYNC: when the unit's lists span more than one page, the pages of every lane's
+      // list (at most two, since the list is shorter than kHub entries) are requested
+      // together before the scan, so that the unit's misses overlap instead of
+      // following one another
+      uint64_t p0 = ((uint64_t)s * 4) / kPage, p1 = dg ? ((uint64_t)(s + dg - 1) * 4) / kPage : p0;
+      unsigned multi = __ballot_sync(kFull, dg && p1 != p0);
+      uint64_t lo = dg ? p0 : ~0ull, hi = dg ? p1 : 0;
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        lo = min(lo, (uint64_t)__shfl_xor_sync(kFull, lo, o));
+        hi = max(hi, (uint64_t)__shfl_xor_sync(kFull, hi, o));
+      }
+      if (hi > lo) {
+        bool w0 = dg && !(pc.valid && pc.page == col_page0 + p0);
+        if (!warp_request_call(d, w0, col_page0 + p0, a.q0, false, a.deadline)) return false;
+        if (multi && !warp_request_call(d, dg && p1 != p0, col_page0 + p1, a.q0, false, a.deadline)) return false;
+      }
+    }
+    return scan_lists(d, a, s, dg, L, found, pc);
   }
 
   // Take queued slices of level L, one ticket (a record index) at a time, until every
