@@ -857,9 +857,11 @@ using BfsApp = BfsAppT<false>;
 // the row's last slice writes y[v].  Every row is therefore the sequential definition
 // bit for bit; only the adds of a long row run one slice after the other.
 //   SYNC : every page when needed.
-//   ASYNC: while the warp computes unit i, the offsets of unit i+1 are read and the
-//          column and value pages of its entries are requested, and the offsets pages
-//          of unit i+2 are requested.
+//   ASYNC: a unit requests the column and value pages of all the entries it sums (at
+//          most 32 of each array) right after reading its offsets, then computes, so
+//          that the unit's misses overlap.  (A pipeline that requested the next units'
+//          pages while computing this one was measured slower with the cache at an
+//          eighth of the arrays: those pages were evicted before their use.)
 // kDirect: the same kernel over a CSR held in device memory (h_off, h_col, h_val),
 // without the cache or the queues (Sec. 4.5 "kernel time").
 template <bool kDirect>
@@ -1105,18 +1107,9 @@ struct SpmvAppT {
     return v0 < n;
   }
 
-  // stage A: request the offsets pages of a unit (its offsets [v0, min(v0+32, n)])
-  __device__ bool stage_a(const Dev &d, const AppCtx &a, uint32_t v0) const {
-    if constexpr (kDirect) return true;
-    uint32_t vend = min(v0 + 32, n);
-    uint64_t pa = off_page0 + ((uint64_t)v0 * 8) / kPage, pb = off_page0 + ((uint64_t)vend * 8) / kPage;
-    bool want = (lane_id() == 0) || (lane_id() == 1 && pb != pa);
-    return warp_request_call(d, want, lane_id() == 0 ? pa : pb, a.q0, false, a.deadline, true);
-  }
-
-  // stage B: read the offsets, queue long rows, request the unit's column and value pages
-  __device__ bool stage_b(const Dev &d, const AppCtx &a, uint32_t v0, int64_t &s, uint32_t &dg, bool &keep,
-                          unsigned long long &entries, Pin &po, Pin &pcol, Pin &pval) const {
+  // ASYNC: read the unit's offsets, queue its long rows, request its column and value pages
+  __device__ bool issue_unit(const Dev &d, const AppCtx &a, uint32_t v0, int64_t &s, uint32_t &dg, bool &keep,
+                             unsigned long long &entries, Pin &po, Pin &pcol, Pin &pval) const {
     uint32_t v = v0 + lane_id();
     bool f = v < n;
     int64_t e = 0;
@@ -1262,24 +1255,13 @@ struct SpmvAppT {
     bool ok = true;
     uint32_t chunk = 0, sub = kChunk;
     if (!kDirect && mode == AGILE_ASYNC) {
-      uint32_t u0 = 0, v1 = 0, v2 = 0;
-      int64_t s0 = 0, s1 = 0;
-      uint32_t dg0 = 0, dg1 = 0;
-      bool k0 = false, k1 = false;
-      bool have0 = false, have1 = next_unit(d, nchunks, chunk, sub, v1), have2 = false;
-      if (have1) ok = stage_a(d, a, v1);
-      while (ok && (have0 || have1)) {
-        have2 = have1 && next_unit(d, nchunks, chunk, sub, v2);
-        if (have2) ok = stage_a(d, a, v2);
-        if (ok && have1) ok = stage_b(d, a, v1, s1, dg1, k1, entries, po, pcol, pval);
-        if (ok && have0) ok = compute_unit(d, a, u0, s0, dg0, k0, po, pcol, pval);
-        have0 = have1;
-        u0 = v1;
-        s0 = s1;
-        dg0 = dg1;
-        k0 = k1;
-        have1 = have2;
-        v1 = v2;
+      uint32_t v0 = 0;
+      while (ok && next_unit(d, nchunks, chunk, sub, v0)) {
+        int64_t s = 0;
+        uint32_t dg = 0;
+        bool k = false;
+        ok = issue_unit(d, a, v0, s, dg, k, entries, po, pcol, pval);
+        if (ok) ok = compute_unit(d, a, v0, s, dg, k, po, pcol, pval);
       }
     } else {
       uint32_t v0 = 0;
