@@ -30,6 +30,11 @@
  *       line pinned for the copy only; a page evicted since its read completed is read
  *       again.  False if the launch timed out.
  *   bool ok = agile::dev::prefetch(d, a, want, page);   // Listing 1 Method-1
+ *   bool ok = agile::dev::get_row(d, a, page, off, nbytes, dst);  // warp-collective
+ *       the synchronous read of a row: bytes [off, off + nbytes) of the page (4-byte
+ *       aligned, within the page) copied to dst, the line pinned for the copy only and
+ *       read from the store first if it is not resident.  False if the launch timed
+ *       out or the arguments are out of range (AGILE_EINVAL, reported by agile_check).
  *
  * a.warp / a.n_warps give the warp's index among the application warps; a.deadline is
  * the launch's own bound (cfg.wait_timeout_ns after the start).
@@ -66,6 +71,10 @@ __device__ __forceinline__ bool copy_page(const Dev &d, const AppCtx &a, uint64_
 }
 __device__ __forceinline__ bool prefetch(const Dev &d, const AppCtx &a, bool want, uint64_t page) {
   return api_prefetch(d, a, want, page);
+}
+__device__ __forceinline__ bool get_row(const Dev &d, const AppCtx &a, uint64_t page, uint32_t off, uint32_t nbytes,
+                                        void *dst) {
+  return api_get_row(d, a, page, off, nbytes, dst);
 }
 
 // Share Table (Sec. 3.4.1; the context needs cfg.share_slots > 0), warp-collective.

@@ -1112,6 +1112,26 @@ static __device__ bool api_copy_page(const Dev &d, const AppCtx &a, uint64_t pag
   return true;
 }
 
+// get_row (the synchronous read of part of a page, warp-collective, uniform arguments):
+// copy bytes [off, off + nbytes) of `page` to dst, the line pinned for the copy only.
+// off, nbytes and dst must be 4-byte aligned and off + nbytes at most one page; else
+// AGILE_EINVAL is recorded and false returned.  False also if the launch timed out.
+static __device__ bool api_get_row(const Dev &d, const AppCtx &a, uint64_t page, uint32_t off, uint32_t nbytes,
+                                   void *dst) {
+  if (((off | nbytes | (uint32_t)(uintptr_t)dst) & 3u) || nbytes > kPage || off > kPage - nbytes) {
+    if (lane_id() == 0) set_error(d, AGILE_EINVAL);
+    return false;
+  }
+  uint32_t line;
+  if (!warp_pin_page<true>(d, page, a.q0, a.deadline, line)) return false;
+  const uint8_t *src = line_ptr(d, line) + off;
+  int32_t *o = (int32_t *)dst;
+  for (uint32_t i = lane_id(); i < nbytes / 4; i += 32) o[i] = ld_cg_s32(src + 4 * i);
+  __syncwarp();
+  if (lane_id() == 0) cache_unpin(d, line);
+  return true;
+}
+
 // prefetch (Listing 1 Method-1): start filling the pages of the lanes with `want`.
 static __device__ bool api_prefetch(const Dev &d, const AppCtx &a, bool want, uint64_t page) {
   return warp_request_call(d, want, page, a.q0, false, a.deadline, true);

@@ -97,3 +97,53 @@ def test_wait_times_out_through_the_token(user_lib):
         c.check()
         assert (status == 0).all() and (pending == 0).all()
         assert np.array_equal(got.reshape(-1), store)
+
+
+@pytest.fixture(scope="module")
+def row_lib():
+    L = build_user_kernel("row_demo")
+    L.row_demo.restype = C.c_int
+    L.row_demo.argtypes = [C.c_void_p] * 4 + [C.c_uint32, C.c_void_p, C.c_uint32, C.c_void_p]
+    return L
+
+
+def _rows(L, c, pages, offs, lens, app_warps=0):
+    n = len(pages)
+    d_pages = torch.from_numpy(np.asarray(pages, dtype=np.uint64).view(np.int64)).to(DEV)
+    d_offs = torch.from_numpy(np.asarray(offs, dtype=np.uint32).view(np.int32)).to(DEV)
+    d_lens = torch.from_numpy(np.asarray(lens, dtype=np.uint32).view(np.int32)).to(DEV)
+    dst = torch.zeros(n * 4096, dtype=torch.uint8, device=DEV)
+    rc = L.row_demo(c.h, d_pages.data_ptr(), d_offs.data_ptr(), d_lens.data_ptr(), n, dst.data_ptr(), app_warps,
+                    c.stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    return dst.cpu().numpy().reshape(n, 4096)
+
+
+def test_get_row_reads_the_bytes_of_the_row(row_lib):
+    # rows of 4-4096 bytes at 4-byte aligned offsets, through a cache of a quarter of the
+    # pages (misses, hits and evictions); the rest of each slot stays untouched
+    npages = 512
+    store = _store(npages, 75)
+    n = 3000
+    pages = synth.uniform_int(76, n, npages)
+    lens = 4 * (synth.uniform_int(77, n, 1024) + 1)
+    offs = 4 * np.array([synth.uniform_int(78 + i, 1, (4096 - int(ln)) // 4 + 1)[0] for i, ln in enumerate(lens)])
+    with Ctx(store.nbytes, cache_bytes=128 * 4096, ways=8, num_queues=16, queue_depth=64) as c:
+        c.put(0, store)
+        got = _rows(row_lib, c, pages, offs, lens)
+        c.check()
+        for i in range(n):
+            p, o, ln = int(pages[i]), int(offs[i]), int(lens[i])
+            assert np.array_equal(got[i, :ln], store[p * 4096 + o:p * 4096 + o + ln]), i
+            assert not got[i, ln:].any(), i
+        assert c.stats()["evictions"] > 0
+
+
+def test_get_row_rejects_a_row_past_the_page(row_lib):
+    store = _store(8, 79)
+    with Ctx(store.nbytes, cache_bytes=8 * 4096, ways=8, num_queues=4, queue_depth=64) as c:
+        c.put(0, store)
+        got = _rows(row_lib, c, [3], [4092], [8], app_warps=1)   # 4 bytes past the page
+        assert not got.any()
+        assert ag.agile_check(c.h) == ag.AGILE_EINVAL
