@@ -658,7 +658,7 @@ struct BfsAppT {
   // instead of following one another.  Only when each lane has at most one page to
   // request (sparse levels): in dense ones the pages would outnumber what the cache
   // holds for the running warps.
-  __device__ bool prefetch_chunk(const Dev &d, const AppCtx &a, uint32_t c0, int32_t L, Pin &pc) const {
+  __device__ bool prefetch_chunk(const Dev &d, const AppCtx &a, uint32_t c0, uint32_t fbits, Pin &pc) const {
     constexpr uint32_t U = kChunk / 32;
     unsigned l = lane_id();
     // the lane's page to request (at most one over the chunk's units; two or more
@@ -667,7 +667,7 @@ struct BfsAppT {
     uint64_t pg = 0;
     for (uint32_t k = 0; k < U; ++k) {
       uint32_t v = c0 + 32 * k + l;
-      bool f = v < n && ld_rlx32((const uint32_t *)&level[v]) == (uint32_t)L;
+      bool f = (fbits >> k) & 1u;
       if (!__any_sync(kFull, f)) continue;
       int64_t s0 = 0, e0 = 0;
       if (!read_offsets(d, a, v, f, s0, e0, pc)) return false;
@@ -685,10 +685,10 @@ struct BfsAppT {
   }
 
   // one 32-vertex unit: SYNC requests every page when needed
-  __device__ bool chunk(const Dev &d, const AppCtx &a, uint32_t v0, int32_t L, uint32_t &found,
+  // (f: the lane's vertex is in the frontier)
+  __device__ bool chunk(const Dev &d, const AppCtx &a, uint32_t v0, bool f, int32_t L, uint32_t &found,
                         unsigned long long &scanned, Pin &pc) const {
     uint32_t v = v0 + lane_id();
-    bool f = v < n && ld_rlx32((const uint32_t *)&level[v]) == (uint32_t)L;
     if (!__any_sync(kFull, f)) return true;
     int64_t s = 0, e = 0;
     if (!read_offsets(d, a, v, f, s, e, pc)) return false;
@@ -808,8 +808,23 @@ struct BfsAppT {
         if (l == 0) c = atomicAdd(&d.run->work[L & 1], 1u);
         c = __shfl_sync(kFull, c, 0);
         if (c >= nchunks || aborted(d)) break;
-        if (!kDirect && mode == AGILE_ASYNC) ok = prefetch_chunk(d, a, c * kChunk, L, pc);
-        for (uint32_t sub = 0; sub < kChunk && ok; sub += 32) ok = chunk(d, a, c * kChunk + sub, L, found, scanned, pc);
+        // the chunk's level words, all in flight together: bit k of fbits says whether
+        // the lane's vertex of unit k is in the frontier (a word equal to L was written
+        // at the level before and does not change during this one)
+        constexpr uint32_t U = kChunk / 32;
+        uint32_t lv[U];
+#pragma unroll
+        for (uint32_t k = 0; k < U; ++k) {
+          uint32_t v = c * kChunk + 32 * k + l;
+          lv[k] = v < n ? ld_rlx32((const uint32_t *)&level[v]) : 0xFFFFFFFFu;
+        }
+        uint32_t fbits = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < U; ++k) fbits |= (lv[k] == (uint32_t)L ? 1u : 0u) << k;
+        if (!__any_sync(kFull, fbits)) continue;
+        if (!kDirect && mode == AGILE_ASYNC) ok = prefetch_chunk(d, a, c * kChunk, fbits, pc);
+        for (uint32_t k = 0; k < U && ok; ++k)
+          ok = chunk(d, a, c * kChunk + 32 * k, (fbits >> k) & 1u, L, found, scanned, pc);
         if (!ok) break;
       }
       // this warp queues no more slices of level L
@@ -1657,12 +1672,18 @@ int agile_embedding_bag(agile_ctx *c, uint64_t table_byte0, uint32_t rows, uint3
   uint32_t warps = std::min<uint32_t>(n_bags, warps_for_cache(c, 4, 32));
   auto go = [&](auto tag) {
     using App = decltype(tag);
-    // rows requested ahead (async) and pin groups are sized by the warps that run
+    // rows requested ahead (async) and pin groups are sized by the warps that run: a
+    // warp's share of the lines holds its pinned group and its lookahead.  With fewer
+    // than 8 lines a warp the cache is too small for a lookahead (Sec. 4.4): a line
+    // requested ahead is evicted for another warp's demand before its use, so the call
+    // runs without one (as SYNC; measured on the 1,024-line cache of the 32 MiB table:
+    // 8.4 M lookups/s with the lookahead, 11.7 M without, the same as SYNC).
     uint32_t run = running_app_warps<App>(c, warps);
-    uint64_t ahead = mode == AGILE_ASYNC ? c->dev.nlines / (2ull * run) : 0;
+    const bool look = mode == AGILE_ASYNC && c->dev.nlines / run >= 8;
+    uint64_t ahead = look ? c->dev.nlines / (2ull * run) : 0;
     ahead = std::max<uint64_t>(1, std::min<uint64_t>(32, ahead * c->cfg.prefetch_depth));
-    App app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, mode, (uint32_t)ahead,
-            pin_group(c, run), list, list_n};
+    App app{table_byte0 / kPage, rows, dim, d_idx, d_offsets, n_bags, d_out, look ? mode : (uint32_t)AGILE_SYNC,
+            (uint32_t)ahead, pin_group(c, run), list, list_n};
     return launch_engine(c, app, stream, warps);
   };
   if (dim <= 128) {
