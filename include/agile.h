@@ -125,7 +125,13 @@ typedef struct {
                                device time that demand leaves idle.  0 = half of the
                                queues (rounded to a multiple of num_devices; none with
                                fewer than 2 per device), AGILE_NO_PREFETCH_QUEUES = none:
-                               every request shares every queue                      */
+                               every request shares every queue.  A call that makes no
+                               request ahead of need (every SYNC call, asyncRead, BFS,
+                               SpMV, serving) uses every queue for demand.  A lookahead
+                               request of an application (embedding bag, pipeline,
+                               backward) is a hint: it is dropped when its first queue
+                               holds more than 3/4 of its depth in flight, or when two
+                               queues of its class are full                          */
 } agile_config;
 #define AGILE_NO_EXTRA_ENGINES 0xFFFFFFFFu
 #define AGILE_NO_PREFETCH_QUEUES 0xFFFFFFFFu
@@ -214,7 +220,13 @@ AGILE_API int agile_invalidate(agile_ctx *ctx, void *stream);
  * dim*4 <= 4096).  d_out[b*dim + d] = sum over i in [d_offsets[b], d_offsets[b+1])
  * of T[d_idx[i]][d], added in increasing i in FP32 (round to nearest, no fusion).
  * d_idx, d_offsets: int64; d_out: n_bags*dim floats.  Indices outside [0, rows) make
- * the call fail with AGILE_EINVAL reported through agile_check. */
+ * the call fail with AGILE_EINVAL reported through agile_check.
+ * The call first sums, in a light kernel, every bag of at most 32 indices whose pages
+ * are all resident; the engine launch then handles the others (scratch for their list
+ * is allocated on first use and kept by the context).  mode AGILE_ASYNC requests the
+ * pages of the rows ahead of the one being summed, while a warp's share of the cache
+ * lines is at least 8; below that the call runs as AGILE_SYNC, since a line requested
+ * ahead would be evicted before its use. */
 AGILE_API int agile_embedding_bag(agile_ctx *ctx, uint64_t table_byte0, uint32_t rows, uint32_t dim,
                         const int64_t *d_idx, const int64_t *d_offsets, uint32_t n_bags,
                         float *d_out, uint32_t mode, void *stream);
