@@ -265,11 +265,12 @@ AGILE_API int agile_embedding_pipeline(agile_ctx *ctx, uint64_t table_byte0, uin
 
 /* Breadth-first search over a CSR graph on the store (Sec. 4.5): int64 offsets
  * [n_vertices+1] at byte offsets_byte0, int32 columns at byte cols_byte0 (both
- * multiples of 4096).  d_level[v] = BFS level of v from src, -1 when unreachable.
- * *d_edges_scanned (uint64, device, may be NULL) = sum of the degrees of every
- * reached vertex.  Top-down, level-synchronous.  AGILE_SYNC requests every page when
- * it is needed; AGILE_ASYNC also requests all pages of a slice of a long adjacency
- * list before scanning it (a warp's own vertices as in AGILE_SYNC). */
+ * multiples of 4096); 0 < n_vertices < 2^31.  d_level[v] = BFS level of v from src,
+ * -1 when unreachable.  *d_edges_scanned (uint64, device, may be NULL) = sum of the
+ * degrees of every reached vertex.  Top-down, level-synchronous.  AGILE_SYNC requests
+ * every page when it is needed; AGILE_ASYNC issues the reads of the work at hand before
+ * it waits for any of them: the list pages of a 32-vertex unit, those of a sparse
+ * chunk's units, and every page of a slice of a long adjacency list. */
 AGILE_API int agile_bfs(agile_ctx *ctx, uint64_t offsets_byte0, uint64_t cols_byte0,
               uint32_t n_vertices, int32_t src, int32_t *d_level,
               uint64_t *d_edges_scanned, uint32_t mode, void *stream);

@@ -1528,7 +1528,7 @@ int bfs_check(agile_ctx *c, uint64_t offsets_byte0, uint64_t cols_byte0, uint32_
               int32_t *d_level, uint32_t mode) {
   if (!c || mode > 1 || !d_level) return AGILE_EINVAL;
   if (offsets_byte0 % kPage || cols_byte0 % kPage) return AGILE_EINVAL;
-  if (n_vertices == 0 || src < 0 || (uint32_t)src >= n_vertices) return AGILE_EINVAL;
+  if (n_vertices == 0 || n_vertices >= (1u << 31) || src < 0 || (uint32_t)src >= n_vertices) return AGILE_EINVAL;
   if (offsets_byte0 + ((uint64_t)n_vertices + 1) * 8 > c->cfg.store_bytes) return AGILE_EINVAL;
   if (cols_byte0 >= c->cfg.store_bytes) return AGILE_EINVAL;
   return AGILE_OK;
@@ -1806,7 +1806,7 @@ int agile_embedding_bag_hbm(agile_ctx *c, const float *d_table, uint32_t rows, u
 int agile_bfs_hbm(agile_ctx *c, const int64_t *d_offsets, const int32_t *d_cols, uint32_t n_vertices,
                   uint64_t n_cols, int32_t src, int32_t *d_level, uint64_t *d_edges_scanned, void *stream) {
   if (!c || !d_offsets || !d_cols || !d_level) return AGILE_EINVAL;
-  if (n_vertices == 0 || src < 0 || (uint32_t)src >= n_vertices) return AGILE_EINVAL;
+  if (n_vertices == 0 || n_vertices >= (1u << 31) || src < 0 || (uint32_t)src >= n_vertices) return AGILE_EINVAL;
   AGILE_CUDA_TRY(cudaSetDevice(c->device));
   int r = ensure_slice_entries(c, n_cols, 1024 / BfsApp::kHub);
   if (r) return r;
