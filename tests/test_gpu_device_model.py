@@ -209,7 +209,9 @@ def test_demand_queues_are_served_before_prefetch_queues():
     stride = 200_000 * dim * 4
     tabs = [np.array(synth.table_normal(70 + k, rows, dim)) for k in range(nt)]
     idx = synth.indices_uniform(72, nt * nbags * pool, rows).reshape(1, nt, nbags, pool)
-    with Ctx(stride * nt, cache_bytes=4096 * 4096, ways=8, num_queues=16, queue_depth=64,
+    # 32 queues of depth 64: room for more than the 32 warps' own groups of 32 rows, so
+    # the asynchronous call keeps its lookahead
+    with Ctx(stride * nt, cache_bytes=4096 * 4096, ways=8, num_queues=32, queue_depth=64,
              emu_device_read_gbps=1.0, trace_records=65536) as c:
         for k in range(nt):
             c.put(k * stride, tabs[k])
@@ -225,6 +227,6 @@ def test_demand_queues_are_served_before_prefetch_queues():
         tr, n = ag.agile_trace(c.h, 65536)
         assert n == tr.size
         wait = tr["t_start"].astype(np.int64) - tr["t_seen"].astype(np.int64)
-        pf = tr["q"] >= 8                      # queues 8..15 carry the prefetches
+        pf = tr["q"] >= 16                     # queues 16..31 carry the prefetches
         assert pf.sum() > 100 and (~pf).sum() > 100
         assert wait[~pf].mean() < wait[pf].mean(), (wait[~pf].mean(), wait[pf].mean())
