@@ -1719,11 +1719,13 @@ int agile_embedding_pipeline(agile_ctx *c, uint64_t table_byte0, uint64_t table_
     uint32_t run = running_app_warps<App>(c, warps);
     const uint32_t group = pin_group(c, run);
     // A lookahead adds requests in flight only while the queues have room for more than
-    // the warps' own demand: when the running warps' groups of rows alone fill the queue
-    // slots, the call runs as SYNC (measured at the full grid of 2,128 warps, where
-    // demand fills the 32 K slots: async 0.93-1.01x sync with the lookahead, its hints
-    // mostly dropped for crowded queues).
-    const bool look = mode == AGILE_ASYNC && (uint64_t)run * group < (uint64_t)c->dev.Q * (c->dev.depth - 1);
+    // the warps' own demand.  The running warps' groups of rows are at most run * group
+    // reads in flight, about half of that while the warps also compute; when that half
+    // alone fills the queue slots, the call runs as SYNC (measured at the full grid of
+    // 2,128 warps: async 0.93-1.01x sync with the lookahead, its hints mostly dropped
+    // for crowded queues).
+    const bool look =
+        mode == AGILE_ASYNC && (uint64_t)run * group < 2ull * c->dev.Q * (c->dev.depth - 1);
     uint64_t ahead = look ? c->dev.nlines / (2ull * run) * c->cfg.prefetch_depth : 0;
     ahead = std::max<uint64_t>(1, std::min<uint64_t>(per_unit, ahead));
     App app{table_byte0 / kPage, table_stride, n_tables, rows, dim, d_idx, pooling, n_bags, n_batches,
